@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Benchmark of the RKAB hot path on GB300.
+
+Workload (default): consistent dense system A 80000 x 10000, iid N(0,1)
+float32, x* iid N(0,1), b = fl32(A x*) (product in FP64), x0 = 0; RKAB with
+q = 132 workers and alpha = n = 10000 projections per worker between
+averages, run until ||x - x*|| / ||x*|| < 1e-6 (checked after every average).
+
+One step = one pass of the whole hot path on resident inputs: the sampling
+tables (rk_setup: exact row weights, prefix sum, alias table, reciprocal
+norms) and the solve to tolerance (draws, projections, averages, checks).
+value = row projections per second over all timed steps (q * alpha * rounds
+per step); ms_per_step = time to tolerance including the setup.
+
+--impl reference times the FP64 CPU oracle on this machine's host cores on a
+bounded sample of the same workload (the reference arm of this build: the
+paper's own implementation is CPU code that is not available here).
+
+Multi-GPU: the path is run as independent replicas (one per rank, no
+collective in the data path); value sums the replicas' projections over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RKAB time-to-1e-6 and row-proj/s, bf16+refine vs fp32 plain, % of HBM peak"
+UNIT = "row-proj/s"
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=80000)
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--q", type=int, default=132)
+    ap.add_argument("--alpha", type=int, default=0, help="projections per worker per round (0: n)")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-rounds", type=int, default=400)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU work of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha1()
+    for f in ("rk_solve.cu", "rk_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2401_17474_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(tag: str):
+    """DRAM bytes per projection recorded by an ncu capture of the current kernel
+    source (profiles/<kernel>_<workload>.txt, line 'traffic_bytes_per_proj <v> src <hash>')."""
+    path = os.path.join(PROFILE_DIR, f"rkab_kernel_{tag}.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("traffic_bytes_per_proj"):
+                    parts = line.split()
+                    if len(parts) >= 4 and parts[3] == kernel_hash():
+                        return float(parts[1])
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(n, q, alpha, rounds, elem=4):
+    """Bytes the method must move: per projection the row (n*elem), b_i, 1/||A_i||^2
+    and the alias entry (thr64 + alias); per round the averaging traffic (write V,
+    read V, reload x in every CTA) ~ 3 q n 4."""
+    per_proj = n * elem + 4 + 4 + 12
+    return rounds * (q * alpha * per_proj + 3 * q * n * 4)
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_sample(A_np, b_np, tab, q, alpha_sample, seed, threads):
+    import numpy as np
+
+    import oracle
+    n = A_np.shape[1]
+    t0 = time.perf_counter()
+    oracle.rkab(A_np, b_np.astype(np.float64), np.zeros(n), q=q, alpha=alpha_sample, rounds=1,
+                seed=seed, tab=tab, threads=threads)
+    dt = time.perf_counter() - t0
+    return q * alpha_sample, dt
+
+
+def cpu_baseline(A_np, b_np, q, seed, target_s):
+    import oracle
+    threads = os.cpu_count() or 1
+    tab = oracle.table(A_np)
+    probe = 20
+    units, dt = oracle_sample(A_np, b_np, tab, q, probe, seed, threads)
+    alpha_s = max(probe, int(probe * target_s / max(dt, 1e-3)))
+    units, dt = oracle_sample(A_np, b_np, tab, q, alpha_s, seed, threads)
+    return {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"1 RKAB round of q={q} workers x alpha={alpha_s} projections "
+                      f"({units} projections, FP64, OpenMP over workers) on the same "
+                      f"{A_np.shape[0]}x{A_np.shape[1]} system; {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import rk_inputs
+    n = args.n
+    s = rk_inputs.gaussian_system(args.m, n, seed=args.seed)
+    threads = os.cpu_count() or 1
+    tab = oracle.table(s.A)
+    probe = 20
+    _, dt = oracle_sample(s.A, s.b, tab, args.q, probe, args.seed, threads)
+    per_step_target = max(1.0, min(20.0, 120.0 / max(args.steps + args.warmup, 1)))
+    alpha_s = max(probe, int(probe * per_step_target / max(dt, 1e-3)))
+    for _ in range(args.warmup):
+        oracle_sample(s.A, s.b, tab, args.q, alpha_s, args.seed, threads)
+    tot_u, tot_t = 0, 0.0
+    for k in range(args.steps):
+        u, dt = oracle_sample(s.A, s.b, tab, args.q, alpha_s, args.seed + k, threads)
+        tot_u += u
+        tot_t += dt
+    val = tot_u / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"rkab_consistent_{args.m}x{n}_q{args.q}", "m": args.m, "n": n,
+                   "q": args.q, "alpha_sample": alpha_s},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"per step 1 RKAB round, q={args.q} x alpha={alpha_s} "
+                                   f"projections (FP64 oracle, OpenMP over workers)"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import rk_inputs
+    import paper_2401_17474_gb300 as rk
+    from paper_2401_17474_gb300 import build as rkbuild
+    rkbuild.build()
+
+    m, n, q = args.m, args.n, args.q
+    alpha = args.alpha or n
+    A, b, xs = rk_inputs.gaussian_system_torch(m, n, seed=args.seed + rank, device=str(dev))
+    x0 = torch.zeros(n, dtype=torch.float32, device=dev)
+    x = torch.empty(n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    setup_ws = torch.empty(rk.api._lib.load().rk_setup_workspace_bytes(m, n), dtype=torch.uint8,
+                           device=dev)
+    plan0 = rk.rk_setup(A, stream=stream, workspace=setup_ws)
+    solver = rk.Solver(plan0, q)
+    opts = rk.make_opts(check_every=1, tol=args.tol, x_ref=xs)
+
+    def step(record=None):
+        plan = rk.rk_setup(A, stream=stream, workspace=setup_ws)
+        solver.plan = plan
+        if record is not None:
+            record[0].record(stream)
+        solver.launch(b, x0, x, alpha, args.max_rounds, args.seed, opts, stream)
+        if record is not None:
+            record[1].record(stream)
+        return plan
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up (also finds the rounds to tolerance)
+    for _ in range(max(args.warmup, 3)):
+        plan = step()
+        info = solver.info(stream)
+        if info.status != 0:
+            raise rk.RkError(info.status, "warm-up solve")
+    rounds = info.rounds_done
+
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    clocks = ClockSampler(vis[local] if local < len(vis) else str(local))
+    launches0 = rk.launch_count()
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    ev0.record(stream)
+    plans = []
+    for k in range(args.steps):
+        plans.append(step(kev[k]))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    launches = rk.launch_count() - launches0
+    total_ms = ev0.elapsed_time(ev1)
+    kern_ms = [a.elapsed_time(bq) for a, bq in kev]
+    info = solver.info(stream)
+    if info.status != 0:
+        raise rk.RkError(info.status, "timed solve")
+    rounds_t = info.rounds_done
+    units = q * alpha * rounds_t * args.steps
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, float(units)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        total_ms_all, units_all = float(tmax[0]), float(t[1])
+    else:
+        total_ms_all, units_all = total_ms, float(units)
+    value = units_all / (total_ms_all / 1e3)
+
+    # roofline of the dominant kernel (the persistent solve), from its own events
+    peak, peak_kind = load_peaks()
+    kmean_s = sum(kern_ms) / len(kern_ms) / 1e3
+    alg = algorithmic_bytes(n, q, alpha, rounds_t)
+    achieved = alg / kmean_s / 1e9
+    traffic_pp = recorded_traffic("c2")
+    traffic = None if traffic_pp is None else traffic_pp * q * alpha * rounds_t
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "rkab_kernel<512,5>", "kernel_ms": 1e3 * kmean_s,
+                "algorithmic_bytes": alg}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        A_h = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+        A_h.copy_(A)
+        b_h = b.cpu().pin_memory()
+        xs_h = xs.cpu().pin_memory()
+        x_h = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        A_d = torch.empty_like(A)
+        b_d = torch.empty_like(b)
+        xs_d = torch.empty_like(xs)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            A_d.copy_(A_h, non_blocking=True)
+            b_d.copy_(b_h, non_blocking=True)
+            xs_d.copy_(xs_h, non_blocking=True)
+            pl = rk.rk_setup(A_d, stream=stream, workspace=setup_ws)
+            solver.plan = pl
+            solver.launch(b_d, x0, x, alpha, args.max_rounds, args.seed,
+                          rk.make_opts(check_every=1, tol=args.tol, x_ref=xs_d), stream)
+            x_h.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = e0.elapsed_time(e1)
+        inf2 = solver.info(stream)
+        e2e = {"value": q * alpha * inf2.rounds_done * e2e_steps / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": A_h.numel() * 4 + b_h.numel() * 4 + xs_h.numel() * 4,
+               "d2h_bytes_per_step": n * 4, "ms_per_step": e_ms / e2e_steps}
+        del A_h, A_d
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        A_np = A.cpu().numpy()
+        b_np = b.cpu().numpy()
+        cpu = cpu_baseline(A_np, b_np, q, args.seed, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"rkab_consistent_{m}x{n}_q{q}_alpha{alpha}_fp32",
+                       "m": m, "n": n, "q": q, "alpha": alpha, "tol": args.tol,
+                       "criterion": "||x-x*||/||x*||, checked after every average",
+                       "rounds_to_tol": rounds_t, "parallelism": f"replicas{ws}",
+                       "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 4 / 1e9),
+                       "time_to_tol_ms": total_ms_all / args.steps,
+                       "solve_ms": 1e3 * kmean_s},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * rkab.h -- C ABI of the GB300 (sm_103a) library for Randomized Kaczmarz (RK),
+ * Randomized Kaczmarz with Averaging (RKA) and the block-averaging variant
+ * RKAB of Ferreira, Acebron and Monteiro, "Parallelization Strategies for the
+ * Randomized Kaczmarz Algorithm on Large-Scale Dense Systems" (arXiv 2401.17474).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Device pointers are CUDA device addresses owned by the caller; the
+ *    library keeps none of them beyond the lifetime documented for the plan
+ *    and never calls cudaMalloc/cudaFree.  Scratch memory is a caller-provided
+ *    workspace whose size is given by the matching *_workspace_bytes query.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Device work is enqueued asynchronously on it; host-side
+ *    argument errors are returned immediately, device-side errors are written
+ *    to a status word in the workspace and reported by rk_plan_status /
+ *    rk_solve_status after the stream has been synchronised.
+ *  - Return value: 0 (RK_OK) or a negative RK_E* code; no exception or
+ *    longjmp crosses the ABI.  rk_strerror() names a code.
+ *  - Matrices are row-major with leading dimension `lda` (elements); the
+ *    base address and lda * element size must be multiples of 16 bytes (rows
+ *    are moved by bulk asynchronous copies).  A holds m * lda elements; the
+ *    columns n .. lda-1 may hold anything.
+ *  - "Round" means one average: every worker applies `alpha` projections to
+ *    its own copy of x, then the q copies are averaged.
+ */
+#ifndef RKAB_H
+#define RKAB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define RK_OK 0
+#define RK_EINVAL (-1)          /* invalid argument (sizes, q, alpha, null pointer, non-finite A) */
+#define RK_EALIGN (-2)          /* base address or lda * element size not a multiple of 16 bytes */
+#define RK_ENOTCORESIDENT (-3)  /* the persistent grid does not fit co-resident on the device */
+#define RK_ETIMEOUT (-4)        /* a device-side wait (grid barrier, copy) exceeded its limit */
+#define RK_EDIVERGED (-5)       /* x became non-finite (e.g. relaxation beyond the stable range) */
+#define RK_ECUDA (-6)           /* a CUDA runtime call failed */
+#define RK_EWORKSPACE (-7)      /* workspace smaller than the size query returned */
+#define RK_ESETUP (-8)          /* the plan's device-side setup failed (see rk_plan_status) */
+
+/* Storage type of the rows the solver streams. */
+typedef enum {
+    RK_F32 = 0,       /* float32 */
+    RK_BF16 = 1,      /* bfloat16, dequantised to float32 on load */
+    RK_FP8E4M3 = 2    /* OCP FP8 e4m3 (finite-only variant) with one float32 scale per row */
+} rk_dtype;
+
+/* Opaque plan: the sampling tables of one matrix, living in a caller workspace. */
+typedef struct rk_plan rk_plan;
+
+/* Solver options.  rk_opts_default() fills the defaults given in brackets. */
+typedef struct {
+    float omega;           /* relaxation of Eq. (alg) (the paper's alpha_i / uniform weight
+                              alpha of Eq. (rka_uni_weights)), in (0, 2)            [1.0] */
+    int64_t check_every;   /* rounds between convergence checks; 0 = never          [1]   */
+    double tol;            /* stop after the first checked round with metric < tol  [0]   */
+    int criterion;         /* 0 none; 1 ||x - x_ref|| / ||x_ref|| (needs x_ref)    [0]   */
+    const float *x_ref;    /* device, n floats: reference solution for criterion 1  [NULL]*/
+    int64_t round0;        /* index of the first round (resume: the draws of a run
+                              restarted at round k equal those of an uninterrupted
+                              run from round k on)                                  [0]   */
+    uint32_t stream_id;    /* Philox stream id of the draws: 0 rows of A, 1 rows of
+                              A^T, 2 recovery solve, 3 + (outer << 8) refinement    [0]   */
+    int same_stream;       /* nonzero: every worker draws worker 0's rows (test hook) [0] */
+    int cluster_size;      /* CTAs per worker: 0 = chosen by the library           [0]   */
+    double timeout_s;      /* limit of every device-side wait, seconds              [10]  */
+} rk_opts;
+
+void rk_opts_default(rk_opts *opts);
+
+/* ------------------------------------------------------------------------ */
+/* Setup: sampling law of Eq. (prob_line), P{i = l} = ||A_l||^2 / ||A||_F^2  */
+/* (Section 2.2), its exclusive prefix sum and its alias table, plus the    */
+/* float32 reciprocals 1/||A_i||^2 used by the projection of Eq. (alg).     */
+/*                                                                          */
+/* The law is encoded with exact integers (identical on every device and on */
+/* the CPU whatever the summation order):                                   */
+/*   e_i  exponent of max_j |a_ij| (max = f 2^e_i, f in [0.5, 1))           */
+/*   R_i  = sum_j floor(a_ij^2 2^(102 - 2 e_i))                             */
+/*   L    = max_i (bitlength(R_i) + 2 e_i - 102) + ceil(log2 m) - 62        */
+/*   K_i  = floor(R_i 2^(2 e_i - 102 - L)),  T = sum_i K_i < 2^62           */
+/*   P_i  = sum_{l < i} K_l (uint64 exclusive prefix)                       */
+/* and the alias table (thr64_i, alias_i) of the law K_i / T is built by    */
+/* the sweeping construction (lights and heavies in ascending index order). */
+/* For RK_BF16 and RK_FP8E4M3 the law and the reciprocals are those of the  */
+/* stored rows: a_ij is the float32 value of the stored element (times the  */
+/* row scale for FP8, rounded to float32).                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace rk_setup needs for an m-row matrix. */
+size_t rk_setup_workspace_bytes(int64_t m, int64_t n);
+
+/* Build a plan for A (device, m x n, row-major, leading dimension lda).
+ *   A          device rows of type dt; must outlive the plan
+ *   row_scale  device, m floats (FP8 only: a_ij = row_scale_i * e4m3_ij); NULL otherwise
+ *   workspace  device, >= rk_setup_workspace_bytes(m, n) bytes, 256-byte aligned; owned by
+ *              the caller, must outlive the plan and not be reused while the plan lives
+ *   out        receives a host-allocated plan (release with rk_plan_destroy)
+ * Limits: 1 <= m < 2^31, 1 <= n < 2^26, lda >= n.  Enqueues the build on `stream`;
+ * an all-zero or non-finite A is reported by rk_plan_status (RK_ESETUP). */
+int rk_setup(const void *A, rk_dtype dt, const float *row_scale, int64_t m, int64_t n,
+             int64_t lda, void *workspace, size_t ws_bytes, void *stream, rk_plan **out);
+
+/* Synchronise `stream` and return the device-side result of the build (RK_OK or
+ * RK_ESETUP); on success *T_out and *L_out (either may be NULL) receive T and L. */
+int rk_plan_status(const rk_plan *plan, void *stream, uint64_t *T_out, int32_t *L_out);
+
+/* Device addresses of the plan's tables (any may be NULL): K (uint64, m), P (uint64, m),
+ * thr64 (uint64, m), alias (uint32, m), inv (float32, m: 1/||A_i||^2, 0 for zero rows). */
+int rk_plan_tables(const rk_plan *plan, const uint64_t **K, const uint64_t **P,
+                   const uint64_t **thr64, const uint32_t **alias, const float **inv);
+
+void rk_plan_destroy(rk_plan *plan);
+
+/* ------------------------------------------------------------------------ */
+/* Sampling: draw of worker `worker`, projection counter t, stream id s:    */
+/* Philox4x32-10 (Salmon et al., SC'11) with key (seed lo, seed hi) and      */
+/* counter (t lo, t hi, worker, s); u = r0 | r1 << 32, u2 = r2 | r3 << 32;   */
+/* bucket c = floor(u m / 2^64); row = c if u2 < thr64_c else alias_c.       */
+/* Worker gamma's j-th projection of round k uses t = k * alpha + j.         */
+/* ------------------------------------------------------------------------ */
+
+/* Test hook: out[k] = draw of (seed, worker, t0 + k, stream_id), k < count (device, uint32). */
+int rk_sample_indices(const rk_plan *plan, uint64_t seed, uint32_t worker, uint32_t stream_id,
+                      uint64_t t0, int64_t count, uint32_t *out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Solve: RKAB, Section 3.4.1 and Algorithm 3.  Each of q workers starts a   */
+/* round from v = x, applies `alpha` projections                            */
+/*   v <- v + omega (b_i - <A_i, v>) / ||A_i||^2 A_i^T      (Eq. (alg))      */
+/* with rows i drawn from Eq. (prob_line), and the round ends with          */
+/*   x <- (1/q) sum_{gamma = 0}^{q-1} v_gamma      (summed in that order).   */
+/* alpha = 1 is RKA, Eq. (rka_uni_weights); q = 1 is RK.                     */
+/* One persistent kernel runs all rounds: every worker is one CTA (or a      */
+/* cluster of CTAs splitting x) that keeps its v on chip and streams the     */
+/* sampled rows from HBM into a ring of shared-memory stages.               */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace one solve with q workers needs. */
+size_t rk_solve_workspace_bytes(const rk_plan *plan, int q);
+
+/* Run `rounds` rounds (fewer if the convergence criterion is met).
+ *   b          device, m floats
+ *   x0         device, n floats: starting point (may alias x)
+ *   x          device, n floats: result
+ *   q          workers, 1 <= q <= the co-resident CTA limit (RK_ENOTCORESIDENT beyond)
+ *   alpha      projections per worker between averages, >= 1
+ *   seed       Philox key
+ *   opts       NULL for defaults
+ *   workspace  device, >= rk_solve_workspace_bytes(plan, q), 256-byte aligned
+ * Asynchronous on `stream`; results (rounds done, last metric, device status) are read
+ * with rk_solve_status.  Calls that share a workspace must not overlap. */
+int rkab_solve(const rk_plan *plan, const float *b, const float *x0, float *x, int q,
+               int64_t alpha, int64_t rounds, uint64_t seed, const rk_opts *opts,
+               void *workspace, size_t ws_bytes, void *stream);
+
+/* rkab_solve with alpha = 1 (RKA of Algorithm 1, Eq. (rka_uni_weights)). */
+int rka_solve(const rk_plan *plan, const float *b, const float *x0, float *x, int q,
+              int64_t rounds, uint64_t seed, const rk_opts *opts, void *workspace,
+              size_t ws_bytes, void *stream);
+
+/* Synchronise `stream` and read the outcome of the last solve that used `workspace`:
+ * returns its device status (RK_OK, RK_ETIMEOUT, RK_EDIVERGED); *rounds_done and
+ * *last_metric (criterion value at the last check, -1 if none) may be NULL. */
+int rk_solve_status(const void *workspace, void *stream, int64_t *rounds_done,
+                    double *last_metric);
+
+/* ------------------------------------------------------------------------ */
+/* Residual of Eq. (system) / Eq. (ls_system) with float32 A and float64     */
+/* accumulation:  r = b - A x,  ||r||_2  and  ||A^T r||_2.                   */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace rk_residual needs. */
+size_t rk_residual_workspace_bytes(int64_t m, int64_t n);
+
+/*   A   device float32 rows (m x n, lda);  b device m floats;  x device n floats
+ *   r   device m doubles (may be NULL)
+ *   norms_out  device, 2 doubles: [||r||, ||A^T r||] (may be NULL; ||A^T r|| costs a
+ *              second pass over A and is computed only when want_atr != 0)
+ * Asynchronous on `stream`. */
+int rk_residual(const float *A, int64_t m, int64_t n, int64_t lda, const float *b,
+                const float *x, double *r, double *norms_out, int want_atr, void *workspace,
+                size_t ws_bytes, void *stream);
+
+/* Name of an error code. */
+const char *rk_strerror(int code);
+
+/* Number of kernel launches this library has enqueued in this process (all entry points). */
+uint64_t rk_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RKAB_H */

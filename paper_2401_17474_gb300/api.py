@@ -1,0 +1,245 @@
+"""Python binding of the RK / RKA / RKAB C ABI (``include/rkab.h``).
+
+Argument marshalling only: torch tensors provide device memory and the
+current CUDA stream; every step of the method runs in the library's kernels.
+Workspaces are allocated here with torch (the library never allocates).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import RkError, RkOpts, check
+
+_DT = {"f32": _lib.RK_F32, "bf16": _lib.RK_BF16, "fp8": _lib.RK_FP8E4M3}
+_ELEM = {"f32": 4, "bf16": 2, "fp8": 1}
+_TORCH_DT = {"f32": torch.float32, "bf16": torch.bfloat16, "fp8": torch.uint8}
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def aligned_rows(A: torch.Tensor, elem: int = 4) -> torch.Tensor:
+    """Copy of the (m, n) matrix A with rows padded to a multiple of 16 bytes
+    (layout only; the padding columns are zero).  Returns A itself when its
+    row stride already qualifies."""
+    if A.stride(1) == 1 and (A.stride(0) * elem) % 16 == 0 and A.data_ptr() % 16 == 0:
+        return A
+    m, n = A.shape
+    per = 16 // elem
+    lda = (n + per - 1) // per * per
+    out = torch.zeros((m, lda), dtype=A.dtype, device=A.device)
+    out[:, :n] = A
+    return out[:, :n]
+
+
+class Plan:
+    """Sampling tables of one matrix (``rk_setup``).  Keeps A, the row scales
+    and the workspace alive as long as the plan lives."""
+
+    def __init__(self, A: torch.Tensor, dtype: str = "f32", row_scale: torch.Tensor | None = None,
+                 stream=None, workspace: torch.Tensor | None = None):
+        L = _lib.load()
+        if dtype not in _DT:
+            raise ValueError(f"dtype must be one of {list(_DT)}")
+        if A.dim() != 2 or not A.is_cuda or A.stride(1) != 1:
+            raise ValueError("A must be a 2-D CUDA tensor with unit column stride")
+        if A.dtype != _TORCH_DT[dtype]:
+            raise ValueError(f"A must have dtype {_TORCH_DT[dtype]} for storage '{dtype}'")
+        self.A = A
+        self.dtype = dtype
+        self.m, self.n = A.shape
+        self.lda = A.stride(0)
+        self.row_scale = row_scale
+        self.device = A.device
+        nbytes = L.rk_setup_workspace_bytes(self.m, self.n)
+        if workspace is not None and workspace.numel() >= nbytes:
+            self.ws = workspace
+        else:
+            self.ws = _workspace(nbytes, A.device)
+        h = ctypes.c_void_p()
+        check(L.rk_setup(_ptr(A), _DT[dtype], _ptr(row_scale), self.m, self.n, self.lda,
+                         _ptr(self.ws), self.ws.numel(), _stream(stream), ctypes.byref(h)),
+              "rk_setup")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def status(self, stream=None):
+        """(T, L) of the law once the device-side build finished (synchronises)."""
+        T = ctypes.c_uint64()
+        Lx = ctypes.c_int32()
+        check(_lib.load().rk_plan_status(self._h, _stream(stream), ctypes.byref(T),
+                                         ctypes.byref(Lx)), "rk_plan_status")
+        return int(T.value), int(Lx.value)
+
+    def tables(self):
+        """Device tensors K (int64 view of uint64), P, thr64, alias (int32 view), inv."""
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        check(_lib.load().rk_plan_tables(self._h, *[ctypes.byref(p) for p in ptrs]),
+              "rk_plan_tables")
+        base = self.ws.data_ptr()
+        m = self.m
+
+        def view(p, nbytes, dt):
+            off = p.value - base
+            return self.ws[off: off + nbytes].view(dt)
+
+        return {
+            "K": view(ptrs[0], 8 * m, torch.int64),
+            "P": view(ptrs[1], 8 * m, torch.int64),
+            "thr64": view(ptrs[2], 8 * m, torch.int64),
+            "alias": view(ptrs[3], 4 * m, torch.int32),
+            "inv": view(ptrs[4], 4 * m, torch.float32),
+        }
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) and self._h.value:
+                _lib.load().rk_plan_destroy(self._h)
+                self._h = ctypes.c_void_p()
+        except Exception:
+            pass
+
+
+def rk_setup(A: torch.Tensor, dtype: str = "f32", row_scale=None, stream=None,
+             workspace=None) -> Plan:
+    """Build the sampling tables of A; `workspace` (uint8 CUDA tensor) is reused when
+    large enough, so repeated setups allocate nothing."""
+    return Plan(A, dtype, row_scale, stream, workspace)
+
+
+def rk_sample_indices(plan: Plan, seed: int, worker: int, t0: int, count: int,
+                      stream_id: int = 0, stream=None) -> torch.Tensor:
+    """Row draws t0 .. t0+count-1 of one worker (uint32 values in an int32 tensor)."""
+    out = torch.empty(max(count, 1), dtype=torch.int32, device=plan.device)
+    check(_lib.load().rk_sample_indices(plan.handle, seed, worker, stream_id, t0, count,
+                                        _ptr(out), _stream(stream)), "rk_sample_indices")
+    return out[:count]
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    rounds_done: int
+    last_metric: float
+
+
+def make_opts(omega=1.0, check_every=1, tol=0.0, x_ref=None, round0=0, stream_id=0,
+              same_stream=False, cluster_size=0, timeout_s=10.0) -> RkOpts:
+    o = RkOpts()
+    _lib.load().rk_opts_default(ctypes.byref(o))
+    o.omega = float(omega)
+    o.check_every = int(check_every)
+    o.tol = float(tol)
+    o.criterion = 1 if x_ref is not None else 0
+    o.x_ref = None if x_ref is None else x_ref.data_ptr()
+    o.round0 = int(round0)
+    o.stream_id = int(stream_id)
+    o.same_stream = int(bool(same_stream))
+    o.cluster_size = int(cluster_size)
+    o.timeout_s = float(timeout_s)
+    return o
+
+
+class Solver:
+    """Reusable solve workspace for one plan and worker count."""
+
+    def __init__(self, plan: Plan, q: int):
+        self.plan = plan
+        self.q = int(q)
+        nbytes = _lib.load().rk_solve_workspace_bytes(plan.handle, self.q)
+        if nbytes == 0:
+            raise RkError(_lib.RK_EINVAL, "rk_solve_workspace_bytes")
+        self.ws = _workspace(nbytes, plan.device)
+
+    def launch(self, b, x0, x, alpha, rounds, seed, opts: RkOpts, stream=None):
+        """Enqueue one rkab_solve (asynchronous)."""
+        check(_lib.load().rkab_solve(self.plan.handle, _ptr(b), _ptr(x0), _ptr(x), self.q,
+                                     int(alpha), int(rounds), int(seed), ctypes.byref(opts),
+                                     _ptr(self.ws), self.ws.numel(), _stream(stream)),
+              "rkab_solve")
+
+    def info(self, stream=None) -> SolveInfo:
+        rd = ctypes.c_int64()
+        lm = ctypes.c_double()
+        st = _lib.load().rk_solve_status(_ptr(self.ws), _stream(stream), ctypes.byref(rd),
+                                         ctypes.byref(lm))
+        return SolveInfo(int(st), int(rd.value), float(lm.value))
+
+
+def _vec(t, n, name):
+    if t is None or not t.is_cuda or t.dtype != torch.float32 or t.numel() != n or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of {n} elements")
+    return t
+
+
+def rkab_solve(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, rounds: int = 1,
+               seed: int = 0, *, omega=1.0, x_ref=None, tol=0.0, check_every=1, round0=0,
+               stream_id=0, same_stream=False, timeout_s=10.0, out=None, solver=None,
+               stream=None, raise_on_error=True):
+    """RKAB solve (alpha projections per worker between averages); returns (x, info)."""
+    b = _vec(b, plan.m, "b")
+    if x0 is None:
+        x0 = torch.zeros(plan.n, dtype=torch.float32, device=plan.device)
+    x0 = _vec(x0, plan.n, "x0")
+    x = out if out is not None else torch.empty(plan.n, dtype=torch.float32, device=plan.device)
+    if x_ref is not None:
+        x_ref = _vec(x_ref, plan.n, "x_ref")
+    s = solver if solver is not None else Solver(plan, q)
+    opts = make_opts(omega, check_every, tol, x_ref, round0, stream_id, same_stream, 0, timeout_s)
+    s.launch(b, x0, x, alpha, rounds, seed, opts, stream)
+    info = s.info(stream)
+    if raise_on_error and info.status != _lib.RK_OK:
+        raise RkError(info.status, "rkab_solve (device)")
+    return x, info
+
+
+def rka_solve(plan: Plan, b, x0=None, q: int = 1, rounds: int = 1, seed: int = 0, **kw):
+    """RKA (alpha = 1): Eq. (rka_uni_weights)."""
+    return rkab_solve(plan, b, x0, q=q, alpha=1, rounds=rounds, seed=seed, **kw)
+
+
+class Residual:
+    def __init__(self, m: int, n: int, device):
+        nbytes = _lib.load().rk_residual_workspace_bytes(m, n)
+        self.ws = _workspace(nbytes, device)
+        self.m, self.n = m, n
+
+    def launch(self, A, b, x, r=None, norms=None, want_atr=True, stream=None):
+        check(_lib.load().rk_residual(_ptr(A), self.m, self.n, A.stride(0), _ptr(b), _ptr(x),
+                                      _ptr(r), _ptr(norms), int(bool(want_atr)), _ptr(self.ws),
+                                      self.ws.numel(), _stream(stream)), "rk_residual")
+
+
+def rk_residual(A: torch.Tensor, b, x, want_atr=True, stream=None):
+    """r = b - A x (float64), and [||r||, ||A^T r||] (float64, device)."""
+    m, n = A.shape
+    if A.dtype != torch.float32 or A.stride(1) != 1:
+        raise ValueError("A must be float32 with unit column stride")
+    b = _vec(b, m, "b")
+    x = _vec(x, n, "x")
+    r = torch.empty(m, dtype=torch.float64, device=A.device)
+    norms = torch.zeros(2, dtype=torch.float64, device=A.device)
+    Residual(m, n, A.device).launch(A, b, x, r, norms, want_atr, stream)
+    return r, norms
+
+
+def launch_count() -> int:
+    """Kernel launches this process has enqueued through the library."""
+    return int(_lib.load().rk_launch_count())

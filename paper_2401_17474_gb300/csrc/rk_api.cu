@@ -1,0 +1,263 @@
+// rk_api.cu -- the extern "C" entry points declared in include/rkab.h:
+// argument checks, workspace layouts, plan lifecycle and status reads.  All
+// device work is in rk_setup.cu, rk_solve.cu and rk_residual.cu.
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <new>
+
+#include "rk_internal.h"
+
+namespace rk {
+
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static size_t elem_bytes(rk_dtype dt) {
+    switch (dt) {
+        case RK_F32: return 4;
+        case RK_BF16: return 2;
+        case RK_FP8E4M3: return 1;
+    }
+    return 0;
+}
+
+size_t setup_ws_bytes(int64_t m) {
+    const size_t M = (size_t)m;
+    return align256(sizeof(SetupInfo))     // info
+           + align256(M * 8) * 3           // K, P, thr64
+           + align256(M * 4) * 2           // alias, inv
+           + align256(M * 16)              // R
+           + align256(M * 4)               // e
+           + align256(M * 4)               // row_pos
+           + align256(M * 16) * 3          // row_Dex, light_Dinc, heavy_Einc
+           + align256(M * 4)               // heavy_idx
+           + align256(scan_tiles_bytes(m)) // scan tile sums
+           + align256(scan_item_bytes());  // scan total
+}
+
+SetupWs setup_ws_carve(void* base, int64_t m) {
+    const size_t M = (size_t)m;
+    uint8_t* p = static_cast<uint8_t*>(base);
+    SetupWs w;
+    auto take = [&](size_t bytes) {
+        uint8_t* q = p;
+        p += align256(bytes);
+        return q;
+    };
+    w.info = reinterpret_cast<SetupInfo*>(take(sizeof(SetupInfo)));
+    w.K = reinterpret_cast<uint64_t*>(take(M * 8));
+    w.P = reinterpret_cast<uint64_t*>(take(M * 8));
+    w.thr64 = reinterpret_cast<uint64_t*>(take(M * 8));
+    w.alias = reinterpret_cast<uint32_t*>(take(M * 4));
+    w.inv = reinterpret_cast<float*>(take(M * 4));
+    w.R = reinterpret_cast<u128*>(take(M * 16));
+    w.e = reinterpret_cast<int*>(take(M * 4));
+    w.row_pos = reinterpret_cast<uint32_t*>(take(M * 4));
+    w.row_Dex = reinterpret_cast<u128*>(take(M * 16));
+    w.light_Dinc = reinterpret_cast<u128*>(take(M * 16));
+    w.heavy_Einc = reinterpret_cast<u128*>(take(M * 16));
+    w.heavy_idx = reinterpret_cast<uint32_t*>(take(M * 4));
+    w.tiles = take(scan_tiles_bytes(m));
+    w.tile_total = take(scan_item_bytes());
+    return w;
+}
+
+}  // namespace rk
+
+using namespace rk;
+
+struct rk_plan {
+    Plan p;
+};
+
+extern "C" {
+
+void rk_opts_default(rk_opts* o) {
+    if (!o) return;
+    o->omega = 1.0f;
+    o->check_every = 1;
+    o->tol = 0.0;
+    o->criterion = 0;
+    o->x_ref = nullptr;
+    o->round0 = 0;
+    o->stream_id = 0;
+    o->same_stream = 0;
+    o->cluster_size = 0;
+    o->timeout_s = 10.0;
+}
+
+const char* rk_strerror(int code) {
+    switch (code) {
+        case RK_OK: return "ok";
+        case RK_EINVAL: return "invalid argument";
+        case RK_EALIGN: return "address or leading dimension not 16-byte aligned";
+        case RK_ENOTCORESIDENT: return "persistent grid does not fit co-resident on the device";
+        case RK_ETIMEOUT: return "device-side wait exceeded its time limit";
+        case RK_EDIVERGED: return "iterate became non-finite";
+        case RK_ECUDA: return "CUDA runtime error";
+        case RK_EWORKSPACE: return "workspace too small";
+        case RK_ESETUP: return "plan setup failed on the device (non-finite or all-zero matrix)";
+        default: return "unknown error";
+    }
+}
+
+uint64_t rk_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+size_t rk_setup_workspace_bytes(int64_t m, int64_t n) {
+    (void)n;
+    if (m < 1) return 0;
+    return setup_ws_bytes(m);
+}
+
+int rk_setup(const void* A, rk_dtype dt, const float* row_scale, int64_t m, int64_t n,
+             int64_t lda, void* workspace, size_t ws_bytes, void* stream, rk_plan** out) {
+    if (!out) return RK_EINVAL;
+    *out = nullptr;
+    if (!A || !workspace || m < 1 || n < 1 || lda < n) return RK_EINVAL;
+    if (m >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 26)) return RK_EINVAL;
+    const size_t eb = elem_bytes(dt);
+    if (eb == 0) return RK_EINVAL;
+    if (dt == RK_FP8E4M3 && !row_scale) return RK_EINVAL;
+    if (!aligned16(A) || ((size_t)lda * eb) % 16 != 0) return RK_EALIGN;
+    if (((uintptr_t)workspace & 255u) != 0) return RK_EALIGN;
+    if (ws_bytes < setup_ws_bytes(m)) return RK_EWORKSPACE;
+    rk_plan* pl = new (std::nothrow) rk_plan;
+    if (!pl) return RK_EINVAL;
+    pl->p.A = A;
+    pl->p.dt = dt;
+    pl->p.row_scale = row_scale;
+    pl->p.m = m;
+    pl->p.n = n;
+    pl->p.lda = lda;
+    pl->p.ws = setup_ws_carve(workspace, m);
+    const int rc = launch_setup(A, dt, row_scale, m, n, lda, pl->p.ws,
+                                static_cast<cudaStream_t>(stream));
+    if (rc != RK_OK) {
+        delete pl;
+        return rc;
+    }
+    *out = pl;
+    return RK_OK;
+}
+
+int rk_plan_status(const rk_plan* plan, void* stream, uint64_t* T_out, int32_t* L_out) {
+    if (!plan) return RK_EINVAL;
+    SetupInfo info;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&info, plan->p.ws.info, sizeof(info), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RK_ECUDA;
+    if (info.status != 0 || info.H == kNoRows || info.T == 0) return RK_ESETUP;
+    if (T_out) *T_out = info.T;
+    if (L_out) *L_out = info.L;
+    return RK_OK;
+}
+
+int rk_plan_tables(const rk_plan* plan, const uint64_t** K, const uint64_t** P,
+                   const uint64_t** thr64, const uint32_t** alias, const float** inv) {
+    if (!plan) return RK_EINVAL;
+    if (K) *K = plan->p.ws.K;
+    if (P) *P = plan->p.ws.P;
+    if (thr64) *thr64 = plan->p.ws.thr64;
+    if (alias) *alias = plan->p.ws.alias;
+    if (inv) *inv = plan->p.ws.inv;
+    return RK_OK;
+}
+
+void rk_plan_destroy(rk_plan* plan) { delete plan; }
+
+int rk_sample_indices(const rk_plan* plan, uint64_t seed, uint32_t worker, uint32_t stream_id,
+                      uint64_t t0, int64_t count, uint32_t* out, void* stream) {
+    if (!plan || count < 0 || (count > 0 && !out)) return RK_EINVAL;
+    return launch_sample_indices(&plan->p, seed, worker, stream_id, t0, count, out,
+                                 static_cast<cudaStream_t>(stream));
+}
+
+size_t rk_solve_workspace_bytes(const rk_plan* plan, int q) {
+    if (!plan || q < 1) return 0;
+    return solve_ws_bytes(&plan->p, q);
+}
+
+int rkab_solve(const rk_plan* plan, const float* b, const float* x0, float* x, int q,
+               int64_t alpha, int64_t rounds, uint64_t seed, const rk_opts* opts,
+               void* workspace, size_t ws_bytes, void* stream) {
+    if (!plan || !b || !x0 || !x || !workspace || q < 1 || alpha < 1 || rounds < 0)
+        return RK_EINVAL;
+    rk_opts o;
+    rk_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(o.omega > 0.0f && o.omega < 2.0f) || o.check_every < 0 || o.round0 < 0 ||
+        !(o.timeout_s > 0.0) || (o.criterion == 1 && !o.x_ref) || o.criterion < 0 ||
+        o.criterion > 1)
+        return RK_EINVAL;
+    if (((uintptr_t)workspace & 255u) != 0) return RK_EALIGN;
+    if (ws_bytes < solve_ws_bytes(&plan->p, q)) return RK_EWORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SolveInfo* info = static_cast<SolveInfo*>(workspace);
+    if (cudaMemsetAsync(info, 0, sizeof(SolveInfo), st) != cudaSuccess) return RK_ECUDA;
+    if (rounds == 0) {
+        if (x != x0 &&
+            cudaMemcpyAsync(x, x0, (size_t)plan->p.n * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return RK_ECUDA;
+        return RK_OK;
+    }
+    SolveArgs a;
+    a.plan = &plan->p;
+    a.b = b;
+    a.x0 = x0;
+    a.x = x;
+    a.q = q;
+    a.alpha = alpha;
+    a.rounds = rounds;
+    a.seed = seed;
+    a.opts = o;
+    a.info = info;
+    const int64_t n4 = (plan->p.n + 3) / 4;
+    a.ldv = n4 * 4;
+    a.V = reinterpret_cast<float*>(static_cast<uint8_t*>(workspace) + align256(sizeof(SolveInfo)));
+    return launch_solve(a, st);
+}
+
+int rka_solve(const rk_plan* plan, const float* b, const float* x0, float* x, int q,
+              int64_t rounds, uint64_t seed, const rk_opts* opts, void* workspace,
+              size_t ws_bytes, void* stream) {
+    return rkab_solve(plan, b, x0, x, q, 1, rounds, seed, opts, workspace, ws_bytes, stream);
+}
+
+int rk_solve_status(const void* workspace, void* stream, int64_t* rounds_done,
+                    double* last_metric) {
+    if (!workspace) return RK_EINVAL;
+    SolveInfo info;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&info, workspace, sizeof(info), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RK_ECUDA;
+    if (rounds_done) *rounds_done = info.rounds_done;
+    if (last_metric) *last_metric = info.last_metric;
+    return info.status;
+}
+
+size_t rk_residual_workspace_bytes(int64_t m, int64_t n) {
+    if (m < 1 || n < 1) return 0;
+    return residual_ws_bytes(m, n);
+}
+
+int rk_residual(const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
+                const float* x, double* r, double* norms_out, int want_atr, void* workspace,
+                size_t ws_bytes, void* stream) {
+    if (!A || !b || !x || !workspace || m < 1 || n < 1 || lda < n) return RK_EINVAL;
+    if (!aligned16(A) || (lda * 4) % 16 != 0 || ((uintptr_t)workspace & 255u) != 0)
+        return RK_EALIGN;
+    if (ws_bytes < residual_ws_bytes(m, n)) return RK_EWORKSPACE;
+    return launch_residual(A, m, n, lda, b, x, r, norms_out, want_atr, workspace,
+                           static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// rk_internal.h -- layouts of the device workspaces and the launchers the
+// C-ABI layer (rk_api.cu) calls.  Not part of the public interface.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rkab.h"
+
+namespace rk {
+
+typedef unsigned __int128 u128;
+
+constexpr int kNoRows = -(1 << 30);  // H before any nonzero row was seen
+
+// Device-side results of the setup (first 256 bytes of the setup workspace).
+struct SetupInfo {
+    int status;      // 0, or RK_EINVAL for non-finite / all-zero A
+    int H;           // max_i bitlength(R_i) + 2 e_i - 102
+    int L;           // H + ceil(log2 m) - 62
+    int pad0;
+    uint64_t T;      // sum_i K_i
+    uint32_t nl, nh; // number of light / heavy buckets
+};
+
+// Pointers into the setup workspace.  The first group is the plan's tables
+// (kept for the solves); the rest is scratch of the build.
+struct SetupWs {
+    SetupInfo* info;
+    uint64_t* K;
+    uint64_t* P;
+    uint64_t* thr64;
+    uint32_t* alias;
+    float* inv;
+    // scratch
+    u128* R;
+    int* e;
+    uint32_t* row_pos;
+    u128* row_Dex;
+    u128* light_Dinc;
+    u128* heavy_Einc;
+    uint32_t* heavy_idx;
+    void* tiles;
+    void* tile_total;
+};
+
+size_t setup_ws_bytes(int64_t m);
+SetupWs setup_ws_carve(void* base, int64_t m);
+size_t scan_tiles_bytes(int64_t m);
+size_t scan_item_bytes();
+
+int launch_setup(const void* A, rk_dtype dt, const float* row_scale, int64_t m, int64_t n,
+                 int64_t lda, const SetupWs& ws, cudaStream_t st);
+
+// Device-side results of a solve (first 256 bytes of the solve workspace).
+struct SolveInfo {
+    int status;
+    int pad0;
+    int64_t rounds_done;
+    double last_metric;
+    unsigned bar_count;
+    unsigned bar_gen;
+};
+
+struct Plan {
+    const void* A;
+    rk_dtype dt;
+    const float* row_scale;
+    int64_t m, n, lda;
+    SetupWs ws;
+};
+
+struct SolveArgs {
+    const Plan* plan;
+    const float* b;
+    const float* x0;
+    float* x;
+    int q;
+    int64_t alpha;
+    int64_t rounds;
+    uint64_t seed;
+    rk_opts opts;
+    SolveInfo* info;
+    float* V;          // q x ldv floats (the workers' iterates before the average)
+    int64_t ldv;
+};
+
+size_t solve_ws_bytes(const Plan* plan, int q);
+int launch_solve(const SolveArgs& a, cudaStream_t st);
+int launch_sample_indices(const Plan* plan, uint64_t seed, uint32_t worker, uint32_t stream_id,
+                          uint64_t t0, int64_t count, uint32_t* out, cudaStream_t st);
+
+size_t residual_ws_bytes(int64_t m, int64_t n);
+int launch_residual(const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
+                    const float* x, double* r, double* norms_out, int want_atr, void* ws,
+                    cudaStream_t st);
+
+void count_launch(int k = 1);
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace rk

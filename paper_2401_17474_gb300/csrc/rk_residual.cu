@@ -1,0 +1,182 @@
+// rk_residual.cu -- residual of Eq. (system) / Eq. (ls_system) with float32 A
+// and float64 accumulation: r = b - A x, ||r||_2 and the normal-equation
+// residual ||A^T r||_2.  All reductions run in a fixed order (warp butterfly,
+// then block partials summed in ascending block order), so results are the
+// same on every run.
+#include <cstdint>
+
+#include "rk_common.cuh"
+#include "rk_internal.h"
+
+namespace rk {
+
+constexpr int kResThreads = 256;
+constexpr int kAtrCols = 1024;  // columns per CTA of the A^T r pass (one float4 per thread)
+
+struct ResWs {
+    double* r;         // m (used when the caller passes no r)
+    double* rr_part;   // per-block sums of r_i^2
+    double* atr_part;  // [row chunks][n]
+    double* norms;     // [2] when the caller passes none
+};
+
+static int res_blocks(int64_t m) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t want = (m + (kResThreads / 32) - 1) / (kResThreads / 32);
+    const int64_t cap = (int64_t)sms * 8;
+    return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+}
+
+static int atr_chunks(int64_t m, int64_t n) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ctiles = (n + kAtrCols - 1) / kAtrCols;
+    int64_t chunks = ((int64_t)sms * 4 + ctiles - 1) / ctiles;
+    if (chunks > m) chunks = m;
+    return (int)(chunks < 1 ? 1 : chunks);
+}
+
+// One warp per row: r_i = b_i - sum_j a_ij x_j, products and sums in float64.
+__global__ void __launch_bounds__(kResThreads) residual_rows_kernel(
+    const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, const float* __restrict__ b,
+    const float* __restrict__ x, double* __restrict__ r, double* __restrict__ rr_part) {
+    __shared__ double s_rr[kResThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n4 = n >> 2;
+    double rr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * (kResThreads / 32) + warp; i < m;
+         i += (int64_t)gridDim.x * (kResThreads / 32)) {
+        const float* a = A + i * lda;
+        const float4* a4 = reinterpret_cast<const float4*>(a);
+        double acc = 0.0;
+        for (int64_t c = lane; c < n4; c += 32) {
+            const float4 v = __ldg(a4 + c);
+            const int64_t j = c * 4;
+            acc = fma((double)v.x, (double)__ldg(x + j), acc);
+            acc = fma((double)v.y, (double)__ldg(x + j + 1), acc);
+            acc = fma((double)v.z, (double)__ldg(x + j + 2), acc);
+            acc = fma((double)v.w, (double)__ldg(x + j + 3), acc);
+        }
+        for (int64_t j = n4 * 4 + lane; j < n; j += 32) acc = fma((double)__ldg(a + j), (double)__ldg(x + j), acc);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const double ri = (double)__ldg(b + i) - acc;
+        if (lane == 0) {
+            r[i] = ri;
+            rr = fma(ri, ri, rr);
+        }
+    }
+    if (lane == 0) s_rr[warp] = rr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kResThreads / 32; ++w) s += s_rr[w];
+        rr_part[blockIdx.x] = s;
+    }
+}
+
+// CTA (column tile, row chunk): partial (A^T r)_j over the chunk's rows, float64.
+__global__ void __launch_bounds__(kResThreads) residual_atr_kernel(
+    const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, const double* __restrict__ r,
+    int chunks, double* __restrict__ atr_part) {
+    const int64_t ctile = blockIdx.x;
+    const int chunk = blockIdx.y;
+    const int64_t rows_per = (m + chunks - 1) / chunks;
+    const int64_t i0 = (int64_t)chunk * rows_per;
+    const int64_t i1 = min(m, i0 + rows_per);
+    const int64_t j0 = ctile * kAtrCols + (int64_t)threadIdx.x * 4;
+    if (j0 >= n) return;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    const bool full4 = (j0 + 3 < n);
+    for (int64_t i = i0; i < i1; ++i) {
+        const double ri = __ldg(r + i);
+        const float* a = A + i * lda + j0;
+        if (full4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(a));
+            a0 = fma(ri, (double)v.x, a0);
+            a1 = fma(ri, (double)v.y, a1);
+            a2 = fma(ri, (double)v.z, a2);
+            a3 = fma(ri, (double)v.w, a3);
+        } else {
+            a0 = fma(ri, (double)__ldg(a), a0);
+            if (j0 + 1 < n) a1 = fma(ri, (double)__ldg(a + 1), a1);
+            if (j0 + 2 < n) a2 = fma(ri, (double)__ldg(a + 2), a2);
+        }
+    }
+    double* out = atr_part + (size_t)chunk * (size_t)n + j0;
+    out[0] = a0;
+    if (j0 + 1 < n) out[1] = a1;
+    if (j0 + 2 < n) out[2] = a2;
+    if (j0 + 3 < n) out[3] = a3;
+}
+
+// One block: norms[0] = sqrt(sum of rr partials), norms[1] = ||A^T r|| from the chunk partials.
+__global__ void __launch_bounds__(kResThreads) residual_finish_kernel(
+    const double* __restrict__ rr_part, int nblocks, const double* __restrict__ atr_part, int chunks,
+    int64_t n, double* __restrict__ norms) {
+    __shared__ double s_part[kResThreads];
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < nblocks; ++k) s += rr_part[k];
+        norms[0] = sqrt(s);
+    }
+    if (!atr_part) return;
+    double acc = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += kResThreads) {
+        double c = 0.0;
+        for (int k = 0; k < chunks; ++k) c += atr_part[(size_t)k * (size_t)n + j];
+        acc = fma(c, c, acc);
+    }
+    s_part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < kResThreads; ++k) s += s_part[k];
+        norms[1] = sqrt(s);
+    }
+}
+
+static ResWs carve(void* base, int64_t m, int64_t n) {
+    uint8_t* p = static_cast<uint8_t*>(base);
+    ResWs w;
+    w.norms = reinterpret_cast<double*>(p);
+    p += 256;
+    w.r = reinterpret_cast<double*>(p);
+    p += align256((size_t)m * 8);
+    w.rr_part = reinterpret_cast<double*>(p);
+    p += align256((size_t)res_blocks(m) * 8);
+    w.atr_part = reinterpret_cast<double*>(p);
+    return w;
+}
+
+size_t residual_ws_bytes(int64_t m, int64_t n) {
+    return 256 + align256((size_t)m * 8) + align256((size_t)res_blocks(m) * 8) +
+           align256((size_t)atr_chunks(m, n) * (size_t)n * 8);
+}
+
+int launch_residual(const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
+                    const float* x, double* r, double* norms_out, int want_atr, void* ws,
+                    cudaStream_t st) {
+    ResWs w = carve(ws, m, n);
+    double* rv = r ? r : w.r;
+    double* norms = norms_out ? norms_out : w.norms;
+    const int nb = res_blocks(m);
+    residual_rows_kernel<<<nb, kResThreads, 0, st>>>(A, m, n, lda, b, x, rv, w.rr_part);
+    count_launch();
+    int chunks = 0;
+    if (want_atr) {
+        chunks = atr_chunks(m, n);
+        dim3 grid((unsigned)((n + kAtrCols - 1) / kAtrCols), (unsigned)chunks);
+        residual_atr_kernel<<<grid, kResThreads, 0, st>>>(A, m, n, lda, rv, chunks, w.atr_part);
+        count_launch();
+    }
+    residual_finish_kernel<<<1, kResThreads, 0, st>>>(w.rr_part, nb, want_atr ? w.atr_part : nullptr,
+                                                      chunks, n, norms);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
+}
+
+}  // namespace rk

@@ -1,0 +1,487 @@
+// rk_setup.cu -- sampling tables of Eq. (prob_line) (Section 2.2) on the GPU:
+// exact integer row weights K_i, their exclusive prefix P_i and total T, the
+// alias table of the law K_i / T (sweeping construction, computed in parallel
+// from prefix sums of the lights' deficits and the heavies' excesses), and the
+// float32 reciprocals 1/||A_i||^2 of the projection of Eq. (alg).
+//
+// Every integer here is exact, so the tables do not depend on the order in
+// which threads add; they equal, bit for bit, those of any implementation of
+// the definitions in rkab.h.
+#include <cstdint>
+#include <cstdio>
+
+#include "rk_internal.h"
+
+namespace rk {
+
+// ---------------------------------------------------------------------------
+// Element loaders: 16-byte chunks of a row decoded to float32.
+// ---------------------------------------------------------------------------
+struct LoadF32 {
+    static constexpr int kPerChunk = 4;
+    static constexpr int kBytes = 4;
+    __device__ static void decode(const uint4& c, float s, float* out) {
+        (void)s;
+        out[0] = __uint_as_float(c.x);
+        out[1] = __uint_as_float(c.y);
+        out[2] = __uint_as_float(c.z);
+        out[3] = __uint_as_float(c.w);
+    }
+};
+
+struct LoadBF16 {
+    static constexpr int kPerChunk = 8;
+    static constexpr int kBytes = 2;
+    __device__ static void decode(const uint4& c, float s, float* out) {
+        (void)s;
+        const uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            out[2 * k] = __uint_as_float(w[k] << 16);
+            out[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+        }
+    }
+};
+
+// OCP FP8 e4m3, finite-only variant: 1 sign, 4 exponent (bias 7), 3 mantissa bits.
+__device__ __forceinline__ float e4m3_to_float(uint32_t code) {
+    const uint32_t sgn = (code & 0x80u) << 24;
+    const uint32_t e = (code >> 3) & 0xFu;
+    const uint32_t f = code & 7u;
+    float v;
+    if (e == 0) {
+        v = (float)f * 0.001953125f;  // f / 8 * 2^-6 = f * 2^-9, exact
+    } else {
+        v = __uint_as_float(((e + 120u) << 23) | (f << 20));  // (1 + f/8) 2^(e-7)
+    }
+    return __uint_as_float(__float_as_uint(v) | sgn);
+}
+
+struct LoadFP8 {
+    static constexpr int kPerChunk = 16;
+    static constexpr int kBytes = 1;
+    __device__ static void decode(const uint4& c, float s, float* out) {
+        const uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) out[4 * k + b] = __fmul_rn(s, e4m3_to_float((w[k] >> (8 * b)) & 0xFFu));
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Row weights: R_i = sum_j floor(a_ij^2 2^(102 - 2 e_i)) exactly, e_i the
+// frexp exponent of max_j |a_ij|; h_i = bitlength(R_i) + 2 e_i - 102 (max -> H);
+// inv_i = 1 / ||A_i||^2 in float32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int frexp_exp_of_absbits(uint32_t ab) {
+    const uint32_t E = ab >> 23;
+    if (E != 0) return (int)E - 126;
+    return (32 - __clz(ab)) - 149;  // subnormal: M 2^-149 with M in [2^(bl-1), 2^bl)
+}
+
+// floor(a^2 2^(102 - 2 e)) for |a| < 2^e, as an exact 128-bit integer.
+__device__ __forceinline__ u128 scaled_square(uint32_t ab, int e) {
+    const uint32_t E = ab >> 23;
+    uint64_t mant;
+    int ex;
+    if (E != 0) {
+        mant = (ab & 0x7FFFFFu) | 0x800000u;
+        ex = (int)E - 150;
+    } else {
+        mant = ab;
+        ex = -149;
+    }
+    const uint64_t sq = mant * mant;  // < 2^48, exact
+    const int s = 2 * ex + 102 - 2 * e;
+    if (s >= 0) return ((u128)sq) << s;
+    if (s <= -64) return 0;
+    return (u128)(sq >> (-s));
+}
+
+__device__ __forceinline__ int bitlen128(u128 v) {
+    const uint64_t hi = (uint64_t)(v >> 64), lo = (uint64_t)v;
+    if (hi) return 128 - __clzll((long long)hi);
+    if (lo) return 64 - __clzll((long long)lo);
+    return 0;
+}
+
+__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int lane_mask) {
+    const uint64_t hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), lane_mask);
+    const uint64_t lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, lane_mask);
+    return ((u128)hi << 64) | lo;
+}
+
+template <class LD>
+__global__ void __launch_bounds__(256) row_weight_kernel(const uint8_t* __restrict__ A,
+                                                         const float* __restrict__ row_scale,
+                                                         int64_t m, int64_t n, int64_t lda_bytes,
+                                                         SetupWs ws) {
+    __shared__ uint32_t s_max[8];
+    __shared__ u128 s_sum[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nchunks = (n + LD::kPerChunk - 1) / LD::kPerChunk;
+    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+        const uint4* row = reinterpret_cast<const uint4*>(A + i * lda_bytes);
+        const float sc = row_scale ? __ldg(row_scale + i) : 1.0f;
+        // pass 1: max |a| as the integer order of the absolute bit patterns
+        uint32_t mx = 0;
+        for (int64_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
+            float v[LD::kPerChunk];
+            LD::decode(__ldg(row + c), sc, v);
+#pragma unroll
+            for (int k = 0; k < LD::kPerChunk; ++k) {
+                if (c * LD::kPerChunk + k < n) mx = max(mx, __float_as_uint(v[k]) & 0x7FFFFFFFu);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_max[warp] = mx;
+        __syncthreads();
+        mx = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, s_max[w]);
+        if (mx >= 0x7F800000u) {  // inf or nan: no law; the row gets zero entries
+            if (threadIdx.x == 0) {
+                atomicCAS(&ws.info->status, 0, RK_EINVAL);
+                ws.R[i] = 0;
+                ws.e[i] = 0;
+                ws.inv[i] = 0.0f;
+            }
+            __syncthreads();
+            continue;
+        }
+        if (mx == 0) {
+            if (threadIdx.x == 0) {
+                ws.R[i] = 0;
+                ws.e[i] = 0;
+                ws.inv[i] = 0.0f;
+            }
+            __syncthreads();
+            continue;
+        }
+        const int e = frexp_exp_of_absbits(mx);
+        // pass 2: exact sum of the scaled squares (the row is now L1/L2 resident)
+        u128 acc = 0;
+        for (int64_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
+            float v[LD::kPerChunk];
+            LD::decode(__ldg(row + c), sc, v);
+#pragma unroll
+            for (int k = 0; k < LD::kPerChunk; ++k) {
+                if (c * LD::kPerChunk + k < n) acc += scaled_square(__float_as_uint(v[k]) & 0x7FFFFFFFu, e);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += shfl_xor_u128(acc, o);
+        if (lane == 0) s_sum[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            u128 R = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) R += s_sum[w];
+            ws.R[i] = R;
+            ws.e[i] = e;
+            const double rd = (double)(uint64_t)(R >> 64) * 18446744073709551616.0 + (double)(uint64_t)R;
+            const double w2 = ldexp(rd, 2 * e - 102);
+            ws.inv[i] = (float)(1.0 / w2);
+            atomicMax(&ws.info->H, bitlen128(R) + 2 * e - 102);
+        }
+        __syncthreads();
+    }
+}
+
+// K_i = R_i >> (L + 102 - 2 e_i); L = H + ceil(log2 m) - 62.
+__global__ void weights_to_k_kernel(int64_t m, SetupWs ws) {
+    const int H = ws.info->H;
+    if (H == kNoRows) {  // all rows zero: no law
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ws.info->status, 0, RK_EINVAL);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+             i += (int64_t)gridDim.x * blockDim.x)
+            ws.K[i] = 0;
+        return;
+    }
+    int c = 0;
+    while (((int64_t)1 << c) < m) ++c;
+    const int L = H + c - 62;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ws.info->L = L;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const u128 R = ws.R[i];
+        uint64_t K = 0;
+        if (R != 0) {
+            const int sh = L + 102 - 2 * ws.e[i];
+            K = (sh >= 128) ? 0 : (uint64_t)(R >> sh);  // sh >= 0 by construction of L
+        }
+        ws.K[i] = K;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exact device-wide exclusive scans over rows (three passes: tile totals, one
+// block over the tile totals, tile rescans).  Integer addition is associative,
+// so the result is the same for any decomposition.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 512;
+constexpr int kScanIpt = 4;
+constexpr int kScanTile = kScanThreads * kScanIpt;
+
+struct ItemK {
+    uint64_t k;
+    __device__ ItemK operator+(const ItemK& o) const { return ItemK{k + o.k}; }
+};
+
+struct ItemC {  // classification: counts of lights / heavies, deficit D and excess E
+    uint32_t nl, nh;
+    u128 D, E;
+    __device__ ItemC operator+(const ItemC& o) const { return ItemC{nl + o.nl, nh + o.nh, D + o.D, E + o.E}; }
+};
+
+struct GetK {
+    const uint64_t* K;
+    __device__ ItemK operator()(int64_t i) const { return ItemK{K[i]}; }
+};
+
+struct PutK {
+    uint64_t* P;
+    __device__ void operator()(int64_t i, const ItemK& excl, const ItemK& own) const {
+        (void)own;
+        P[i] = excl.k;
+    }
+};
+
+__device__ __forceinline__ ItemC classify(const uint64_t* K, int64_t i, uint64_t m, uint64_t T) {
+    const u128 S = (u128)m * (u128)K[i];
+    const u128 TT = (u128)T;
+    if (S < TT) return ItemC{1u, 0u, TT - S, 0};
+    if (S > TT) return ItemC{0u, 1u, 0, S - TT};
+    return ItemC{0u, 0u, 0, 0};
+}
+
+struct GetC {
+    const uint64_t* K;
+    uint64_t m;
+    const SetupInfo* info;
+    __device__ ItemC operator()(int64_t i) const { return classify(K, i, m, info->T); }
+};
+
+// Compaction: light k -> its inclusive deficit prefix; heavy p -> its row and inclusive excess.
+struct PutC {
+    SetupWs ws;
+    __device__ void operator()(int64_t i, const ItemC& excl, const ItemC& own) const {
+        if (own.nl) {
+            ws.light_Dinc[excl.nl] = excl.D + own.D;
+            ws.row_pos[i] = excl.nl;
+            ws.row_Dex[i] = excl.D;
+        } else if (own.nh) {
+            ws.heavy_idx[excl.nh] = (uint32_t)i;
+            ws.heavy_Einc[excl.nh] = excl.E + own.E;
+            ws.row_pos[i] = excl.nh;
+        }
+    }
+};
+
+template <class Item>
+__device__ Item block_exclusive_scan(Item v, Item* sm, Item& total) {
+    // Hillis-Steele inclusive scan in shared memory, then shift.
+    const int t = threadIdx.x;
+    sm[t] = v;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        Item add = v;
+        const bool has = t >= off;
+        if (has) add = sm[t - off];
+        __syncthreads();
+        if (has) v = add + v;
+        sm[t] = v;
+        __syncthreads();
+    }
+    total = sm[blockDim.x - 1];
+    Item ex = (t > 0) ? sm[t - 1] : Item{};
+    __syncthreads();
+    return ex;
+}
+
+template <class Item, class Get>
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(int64_t m, Get get, Item* tile_sums) {
+    __shared__ Item sm[kScanThreads];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanIpt;
+    Item acc{};
+#pragma unroll
+    for (int k = 0; k < kScanIpt; ++k) {
+        if (base + k < m) acc = acc + get(base + k);
+    }
+    Item total;
+    block_exclusive_scan(acc, sm, total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the tile totals in place; grand total to *total_out.
+template <class Item>
+__global__ void __launch_bounds__(kScanThreads) scan_tile_sums_kernel(Item* tile_sums, int64_t ntiles, Item* total_out) {
+    __shared__ Item sm[kScanThreads];
+    const int64_t per = (ntiles + kScanThreads - 1) / kScanThreads;
+    const int64_t lo = (int64_t)threadIdx.x * per;
+    const int64_t hi = min(ntiles, lo + per);
+    Item acc{};
+    for (int64_t k = lo; k < hi; ++k) acc = acc + tile_sums[k];
+    Item total;
+    Item run = block_exclusive_scan(acc, sm, total);
+    for (int64_t k = lo; k < hi; ++k) {
+        const Item v = tile_sums[k];
+        tile_sums[k] = run;
+        run = run + v;
+    }
+    if (threadIdx.x == 0) *total_out = total;
+}
+
+template <class Item, class Get, class Put>
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(int64_t m, Get get, Put put, const Item* tile_offsets) {
+    __shared__ Item sm[kScanThreads];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanIpt;
+    Item own[kScanIpt];
+    Item acc{};
+#pragma unroll
+    for (int k = 0; k < kScanIpt; ++k) {
+        own[k] = (base + k < m) ? get(base + k) : Item{};
+        acc = acc + own[k];
+    }
+    Item total;
+    Item run = block_exclusive_scan(acc, sm, total);
+    run = tile_offsets[blockIdx.x] + run;
+#pragma unroll
+    for (int k = 0; k < kScanIpt; ++k) {
+        if (base + k < m) put(base + k, run, own[k]);
+        run = run + own[k];
+    }
+}
+
+__global__ void store_totals_kernel(SetupWs ws, const ItemK* ktot, const ItemC* ctot) {
+    if (ktot) {
+        ws.info->T = ktot->k;
+        if (ktot->k == 0 && ws.info->status == 0) ws.info->status = RK_EINVAL;
+    }
+    if (ctot) {
+        ws.info->nl = ctot->nl;
+        ws.info->nh = ctot->nh;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Alias table from the prefix sums (the parallel form of the sweep):
+//  light at position k (exclusive deficit D_k): alias = heavy p with the
+//    smallest inclusive excess E_p >= D_k; thr = S_i;
+//  heavy at position p < nh-1: k* = first light with inclusive deficit > E_p;
+//    thr = T + E_p - Dinc_{k*}, alias = heavy p+1;  the last heavy: thr = T, self;
+//  S_i = T: thr = T, self.
+// thr64 = floor(thr 2^64 / T), or UINT64_MAX when thr = T.
+// ---------------------------------------------------------------------------
+__global__ void alias_kernel(int64_t m, SetupWs ws) {
+    if (ws.info->status != 0) return;
+    const uint64_t T = ws.info->T;
+    const uint32_t nl = ws.info->nl, nh = ws.info->nh;
+    const u128 TT = (u128)T;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const u128 S = (u128)(uint64_t)m * (u128)ws.K[i];
+        u128 thr;
+        uint32_t al;
+        if (S < TT) {
+            if (nh == 0) {  // impossible for a valid law; never index an empty list
+                atomicCAS(&ws.info->status, 0, RK_EINVAL);
+                continue;
+            }
+            const u128 D = ws.row_Dex[i];
+            uint32_t lo = 0, hi = nh;  // first p with heavy_Einc[p] >= D
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (ws.heavy_Einc[mid] >= D) hi = mid; else lo = mid + 1;
+            }
+            if (lo >= nh) { atomicCAS(&ws.info->status, 0, RK_EINVAL); lo = nh - 1; }
+            thr = S;
+            al = ws.heavy_idx[lo];
+        } else if (S > TT) {
+            const uint32_t p = ws.row_pos[i];
+            if (p + 1 == nh) {
+                thr = TT;
+                al = (uint32_t)i;
+            } else if (nl == 0 || p >= nh) {  // impossible for a valid law
+                atomicCAS(&ws.info->status, 0, RK_EINVAL);
+                continue;
+            } else {
+                const u128 E = ws.heavy_Einc[p];
+                uint32_t lo = 0, hi = nl;  // first k with light_Dinc[k] > E
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (ws.light_Dinc[mid] > E) hi = mid; else lo = mid + 1;
+                }
+                if (lo >= nl) { atomicCAS(&ws.info->status, 0, RK_EINVAL); lo = nl - 1; }
+                thr = TT + E - ws.light_Dinc[lo];
+                al = ws.heavy_idx[p + 1];
+            }
+        } else {
+            thr = TT;
+            al = (uint32_t)i;
+        }
+        ws.thr64[i] = (thr >= TT) ? ~0ull : (uint64_t)((thr << 64) / TT);
+        ws.alias[i] = al;
+    }
+}
+
+static int grid_for(int64_t m, int threads) {
+    int64_t g = (m + threads - 1) / threads;
+    if (g > 65535LL * 8) g = 65535LL * 8;
+    return (int)(g < 1 ? 1 : g);
+}
+
+int launch_setup(const void* A, rk_dtype dt, const float* row_scale, int64_t m, int64_t n,
+                 int64_t lda, const SetupWs& ws, cudaStream_t st) {
+    cudaMemsetAsync(ws.info, 0, sizeof(SetupInfo), st);
+    SetupInfo init{};
+    init.H = kNoRows;
+    cudaMemcpyAsync(ws.info, &init, sizeof(SetupInfo), cudaMemcpyHostToDevice, st);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int gw = (int)std::min<int64_t>(m, (int64_t)sms * 8);
+    const uint8_t* Ab = static_cast<const uint8_t*>(A);
+    switch (dt) {
+        case RK_F32:
+            row_weight_kernel<LoadF32><<<gw, 256, 0, st>>>(Ab, nullptr, m, n, lda * 4, ws);
+            break;
+        case RK_BF16:
+            row_weight_kernel<LoadBF16><<<gw, 256, 0, st>>>(Ab, nullptr, m, n, lda * 2, ws);
+            break;
+        case RK_FP8E4M3:
+            row_weight_kernel<LoadFP8><<<gw, 256, 0, st>>>(Ab, row_scale, m, n, lda, ws);
+            break;
+    }
+    count_launch();
+    weights_to_k_kernel<<<grid_for(m, 256), 256, 0, st>>>(m, ws);
+    count_launch();
+    const int64_t ntiles = (m + kScanTile - 1) / kScanTile;
+    ItemK* ktiles = reinterpret_cast<ItemK*>(ws.tiles);
+    ItemK* ktot = reinterpret_cast<ItemK*>(ws.tile_total);
+    scan_tiles_kernel<ItemK, GetK><<<(unsigned)ntiles, kScanThreads, 0, st>>>(m, GetK{ws.K}, ktiles);
+    scan_tile_sums_kernel<ItemK><<<1, kScanThreads, 0, st>>>(ktiles, ntiles, ktot);
+    scan_apply_kernel<ItemK, GetK, PutK><<<(unsigned)ntiles, kScanThreads, 0, st>>>(m, GetK{ws.K}, PutK{ws.P}, ktiles);
+    store_totals_kernel<<<1, 1, 0, st>>>(ws, ktot, nullptr);
+    count_launch(4);
+    ItemC* ctiles = reinterpret_cast<ItemC*>(ws.tiles);
+    ItemC* ctot = reinterpret_cast<ItemC*>(ws.tile_total);
+    GetC getc{ws.K, (uint64_t)m, ws.info};
+    scan_tiles_kernel<ItemC, GetC><<<(unsigned)ntiles, kScanThreads, 0, st>>>(m, getc, ctiles);
+    scan_tile_sums_kernel<ItemC><<<1, kScanThreads, 0, st>>>(ctiles, ntiles, ctot);
+    scan_apply_kernel<ItemC, GetC, PutC><<<(unsigned)ntiles, kScanThreads, 0, st>>>(m, getc, PutC{ws}, ctiles);
+    store_totals_kernel<<<1, 1, 0, st>>>(ws, nullptr, ctot);
+    alias_kernel<<<grid_for(m, 256), 256, 0, st>>>(m, ws);
+    count_launch(5);
+    return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
+}
+
+size_t scan_tiles_bytes(int64_t m) {
+    const int64_t ntiles = (m + kScanTile - 1) / kScanTile;
+    return (size_t)ntiles * sizeof(ItemC);
+}
+
+size_t scan_item_bytes() { return sizeof(ItemC); }
+
+}  // namespace rk

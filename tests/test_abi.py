@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads, and exports every function the public
+header declares; the Python binding declares exactly those.  No device work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rkab.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b([a-z_][a-z0-9_]*)\s*\([^;{]*\)\s*;", text)
+    return sorted(set(n for n in names if n.startswith(("rk", "rka", "rkab"))))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2401_17474_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path), path
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("rk_setup", "rka_solve", "rkab_solve", "rk_residual", "rk_sample_indices",
+                 "rk_setup_workspace_bytes", "rk_solve_workspace_bytes", "rk_strerror"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    L, path = lib
+    for name in _declared():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True)
+    exported = set(re.findall(r"\s[TW]\s+(\S+)$", out.stdout, flags=re.M))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_declares_exactly_the_header(lib):
+    from paper_2401_17474_gb300 import _lib
+    assert sorted(_lib.declared_functions()) == _declared()
+
+
+def test_host_side_queries_need_no_device(lib):
+    from paper_2401_17474_gb300 import _lib
+    L = _lib.load()
+    assert L.rk_setup_workspace_bytes(1000, 10) > 1000 * 32
+    assert L.rk_setup_workspace_bytes(0, 10) == 0
+    assert L.rk_strerror(-4) == b"device-side wait exceeded its time limit"
+    o = _lib.RkOpts()
+    L.rk_opts_default(ctypes.byref(o))
+    assert o.omega == 1.0 and o.check_every == 1 and o.timeout_s == 10.0
+    # argument checks fail before any device work
+    h = ctypes.c_void_p()
+    assert L.rk_setup(None, 0, None, 10, 10, 10, None, 0, None, ctypes.byref(h)) == _lib.RK_EINVAL
+    assert L.rk_setup(ctypes.c_void_p(16), 0, None, 10, 10, 12, ctypes.c_void_p(256), 0, None,
+                      ctypes.byref(h)) == _lib.RK_EWORKSPACE
+    assert L.rk_setup(ctypes.c_void_p(16), 0, None, 10, 10, 10, ctypes.c_void_p(256), 1 << 30, None,
+                      ctypes.byref(h)) == _lib.RK_EALIGN      # lda*4 = 40 not a multiple of 16
+    assert L.rkab_solve(None, None, None, None, 1, 1, 1, 0, None, None, 0, None) == _lib.RK_EINVAL

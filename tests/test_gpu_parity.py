@@ -1,0 +1,239 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Integer work (sampling tables, row draws) must be bit-exact; x must
+be within 1e-4 relative (FP32 kernel vs FP64 oracle).
+
+Tolerance: each projection and the average are non-expansive maps
+(Section 2.1), so FP32 rounding differences do not grow along the
+trajectory; the FP32 unit roundoff (6e-8) times the contraction horizon of
+the 2000 x 100 system (1/s_min ~ 170 projections) bounds the drift near 1e-5,
+inside the 1e-4 bar."""
+import numpy as np
+import pytest
+
+import oracle
+import rk_inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def rk():
+    import paper_2401_17474_gb300 as rk_
+    from paper_2401_17474_gb300 import build
+    build.build()
+    return rk_
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _padded(A_np, rk):
+    return rk.aligned_rows(_dev(A_np))
+
+
+def _check_tables(rk, A_np, plan=None):
+    tab = oracle.table(A_np)
+    if plan is None:
+        plan = rk.rk_setup(_padded(A_np, rk))
+    T, L = plan.status()
+    assert (T, L) == (tab.T, tab.L)
+    t = plan.tables()
+    K = t["K"].cpu().numpy().view(np.uint64)
+    P = t["P"].cpu().numpy().view(np.uint64)
+    thr = t["thr64"].cpu().numpy().view(np.uint64)
+    al = t["alias"].cpu().numpy().view(np.uint32)
+    assert np.array_equal(K, tab.K)
+    P_ref = np.concatenate([[0], np.cumsum(tab.K[:-1], dtype=np.uint64)]).astype(np.uint64)
+    assert np.array_equal(P, P_ref)
+    assert np.array_equal(thr, tab.thr64)
+    assert np.array_equal(al, tab.alias)
+    inv = t["inv"].cpu().numpy()
+    w = oracle.row_norms(A_np)
+    nz = w > 0
+    np.testing.assert_allclose(inv[nz], (1.0 / w[nz]).astype(np.float32), rtol=2e-7)
+    assert np.all(inv[~nz] == 0)
+    return plan, tab
+
+
+@pytest.mark.parametrize("case", ["c1", "skewed", "ragged", "zerorows", "onerow", "onecol", "tiny_values"])
+def test_tables_bit_exact(rk, case):
+    rng = np.random.default_rng(21)
+    if case == "c1":
+        A = rk_inputs.gaussian_system(2000, 100, seed=0).A
+    elif case == "skewed":
+        A = rk_inputs.gaussian_system(5000, 64, seed=1, row_scale_decades=2.0).A
+    elif case == "ragged":
+        A = rng.standard_normal((3001, 37)).astype(np.float32)
+    elif case == "zerorows":
+        A = rng.standard_normal((777, 20)).astype(np.float32)
+        A[::5] = 0
+    elif case == "onerow":
+        A = rng.standard_normal((1, 9)).astype(np.float32)
+    elif case == "onecol":
+        A = rng.standard_normal((513, 1)).astype(np.float32)
+    else:
+        A = (rng.standard_normal((300, 12)) * 1e-41).astype(np.float32)  # subnormals
+        A[3] *= np.float32(1e30)
+    _check_tables(rk, A)
+
+
+def test_setup_rejects_zero_and_nonfinite(rk):
+    A = torch.zeros((64, 8), device="cuda")
+    plan = rk.rk_setup(A)
+    with pytest.raises(rk.RkError):
+        plan.status()
+    B = torch.randn((64, 8), device="cuda")
+    B[7, 3] = float("nan")
+    plan = rk.rk_setup(B)
+    with pytest.raises(rk.RkError):
+        plan.status()
+
+
+def test_row_draws_bit_exact(rk):
+    s = rk_inputs.gaussian_system(2000, 100, seed=0)
+    plan, tab = _check_tables(rk, s.A)
+    for worker, t0, count, stream in [(0, 0, 20000, 0), (3, 12345, 5000, 0), (131, 0, 4000, 1),
+                                      (7, (1 << 32) - 100, 300, 2), (1, 1 << 40, 100, 3 | (5 << 8))]:
+        got = rk.rk_sample_indices(plan, 0xDEADBEEF12345, worker, t0, count, stream).cpu().numpy()
+        want = oracle.sample_rows(tab, 0xDEADBEEF12345, worker, t0, count, stream)
+        assert np.array_equal(got.astype(np.int64), want), (worker, t0)
+
+
+def _rel(xg, xo):
+    return np.linalg.norm(xg.astype(np.float64) - xo) / max(np.linalg.norm(xo), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def c1(rk):
+    s = rk_inputs.gaussian_system(2000, 100, seed=0)
+    plan = rk.rk_setup(_dev(s.A))
+    return s, plan, oracle.table(s.A), _dev(s.b)
+
+
+@pytest.mark.parametrize("q", [1, 4])
+@pytest.mark.parametrize("k", [1, 10, 100, 1000, 20000])
+def test_c1_rk_and_rka_match_oracle(rk, c1, q, k):
+    """2000 x 100, x0 = 0, seed 0: RK (q=1) and RKA (q=4, alpha=1) after k rounds."""
+    s, plan, tab, b = c1
+    x, info = rk.rkab_solve(plan, b, q=q, alpha=1, rounds=k, seed=0, check_every=0)
+    assert info.status == 0
+    xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=q, alpha=1, rounds=k, seed=0,
+                     tab=tab)
+    assert _rel(x.cpu().numpy(), xo) < TOL
+
+
+@pytest.mark.parametrize("m,n,q,alpha,rounds,omega", [
+    (3001, 37, 3, 7, 20, 1.0),       # ragged n (tail of a float4), several stages
+    (5000, 300, 8, 50, 6, 1.5),      # relaxation
+    (4000, 1000, 16, 40, 4, 1.0),    # 128-thread CTAs, wider rows
+    (6000, 2600, 5, 30, 3, 0.8),     # 512-thread CTAs
+    (800, 5, 2, 3, 50, 1.0),         # n < 8
+])
+def test_rkab_matches_oracle(rk, m, n, q, alpha, rounds, omega):
+    s = rk_inputs.gaussian_system(m, n, seed=m + n)
+    A = _padded(s.A, rk)
+    plan = rk.rk_setup(A)
+    tab = oracle.table(s.A)
+    x0 = np.random.default_rng(1).standard_normal(n).astype(np.float32)
+    x, info = rk.rkab_solve(plan, _dev(s.b), _dev(x0), q=q, alpha=alpha, rounds=rounds, seed=77,
+                            omega=omega)
+    assert info.status == 0 and info.rounds_done == rounds
+    xo = oracle.rkab(s.A, s.b.astype(np.float64), x0.astype(np.float64), q=q, alpha=alpha,
+                     rounds=rounds, seed=77, tab=tab, omega=omega)
+    assert _rel(x.cpu().numpy(), xo) < TOL
+
+
+def test_special_cases_on_gpu(rk, c1):
+    s, plan, tab, b = c1
+    # q = 1 RKAB with alpha = 30 is RK over 30 * rounds projections
+    x1, _ = rk.rkab_solve(plan, b, q=1, alpha=30, rounds=5, seed=3)
+    xo = oracle.rk(s.A, s.b.astype(np.float64), np.zeros(100), 150, 3, tab)
+    assert _rel(x1.cpu().numpy(), xo) < TOL
+    # all workers on one stream average identical iterates: equals RK
+    x2, _ = rk.rkab_solve(plan, b, q=6, alpha=30, rounds=5, seed=3, same_stream=True)
+    assert _rel(x2.cpu().numpy(), xo) < TOL
+    # rounds = 0 returns x0
+    x0 = torch.randn(100, device="cuda")
+    x3, _ = rk.rkab_solve(plan, b, x0, q=2, alpha=4, rounds=0, seed=1)
+    assert torch.equal(x3, x0)
+
+
+def test_resume_is_bit_identical(rk, c1):
+    s, plan, tab, b = c1
+    full, _ = rk.rkab_solve(plan, b, q=4, alpha=9, rounds=12, seed=5)
+    part, _ = rk.rkab_solve(plan, b, q=4, alpha=9, rounds=5, seed=5)
+    rest, _ = rk.rkab_solve(plan, b, part.clone(), q=4, alpha=9, rounds=7, seed=5, round0=5)
+    assert torch.equal(full, rest)
+    again, _ = rk.rkab_solve(plan, b, q=4, alpha=9, rounds=12, seed=5)
+    assert torch.equal(full, again)   # deterministic run to run
+
+
+def test_x_may_alias_x0(rk, c1):
+    s, plan, tab, b = c1
+    x0 = torch.randn(100, device="cuda")
+    ref, _ = rk.rkab_solve(plan, b, x0.clone(), q=3, alpha=5, rounds=4, seed=2)
+    buf = x0.clone()
+    rk.rkab_solve(plan, b, buf, q=3, alpha=5, rounds=4, seed=2, out=buf)
+    assert torch.equal(buf, ref)
+
+
+def test_stop_rule_matches_oracle(rk, c1):
+    s, plan, tab, b = c1
+    xs = _dev(s.x_star)
+    x, info = rk.rkab_solve(plan, b, q=4, alpha=20, rounds=5000, seed=0, x_ref=xs, tol=1e-5)
+    _, done_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=4, alpha=20,
+                            rounds=5000, seed=0, tab=tab, x_ref=s.x_star.astype(np.float64),
+                            tol=1e-5)
+    assert abs(info.rounds_done - done_o) <= 1
+    assert info.last_metric < 1e-5
+    assert _rel(x.cpu().numpy(), s.x_star.astype(np.float64)) < 1.2e-5
+
+
+def test_argument_errors(rk, c1):
+    s, plan, tab, b = c1
+    with pytest.raises(rk.RkError):
+        rk.rkab_solve(plan, b, q=0, alpha=1, rounds=1)
+    with pytest.raises(rk.RkError):
+        rk.rkab_solve(plan, b, q=2, alpha=1, rounds=1, omega=2.0)
+    with pytest.raises(rk.RkError) as e:
+        rk.rkab_solve(plan, b, q=100000, alpha=1, rounds=1)
+    assert e.value.code == -3   # not co-resident: refused before launch
+
+
+def test_residual_matches_oracle(rk):
+    s = rk_inputs.gaussian_system(3000, 37, seed=3, noise=0.1)
+    A = _padded(s.A, rk)
+    x = np.random.default_rng(2).standard_normal(37).astype(np.float32)
+    r, norms = rk.rk_residual(A, _dev(s.b), _dev(x))
+    ro, rn, an = oracle.residual(s.A, s.b, x.astype(np.float64))
+    scale = np.abs(s.b).max() + np.abs(s.A).sum(axis=1).max() * np.abs(x).max()
+    np.testing.assert_allclose(r.cpu().numpy(), ro, rtol=0, atol=1e-13 * scale)
+    nn = norms.cpu().numpy()
+    assert abs(nn[0] - rn) <= 1e-12 * rn and abs(nn[1] - an) <= 1e-10 * (an + 1e-300)
+
+
+@pytest.mark.slow
+def test_full_size_sampled_parity(rk):
+    """80000 x 10000 (3.2 GB), the launch configuration of the benchmark
+    (q = 132, alpha = n): bit-exact tables and draws, one short round of every
+    worker against the oracle, and convergence of the full solve to 1e-6."""
+    m, n, q = 80000, 10000, 132
+    s = rk_inputs.gaussian_system(m, n, seed=0)
+    A = _dev(s.A)
+    plan, tab = _check_tables(rk, s.A, rk.rk_setup(A))
+    for g in (0, 1, 65, 131):
+        got = rk.rk_sample_indices(plan, 0, g, 10_000 * 7, 10_000).cpu().numpy()
+        assert np.array_equal(got.astype(np.int64), oracle.sample_rows(tab, 0, g, 70_000, 10_000))
+    b = _dev(s.b)
+    x, info = rk.rkab_solve(plan, b, q=q, alpha=10, rounds=1, seed=0)
+    xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(n), q=q, alpha=10, rounds=1, seed=0,
+                     tab=tab, threads=8)
+    assert _rel(x.cpu().numpy(), xo) < TOL
+    xs = _dev(s.x_star)
+    x, info = rk.rkab_solve(plan, b, q=q, alpha=n, rounds=400, seed=0, x_ref=xs, tol=1e-6)
+    assert info.status == 0 and info.last_metric < 1e-6, info
+    assert _rel(x.cpu().numpy(), s.x_star.astype(np.float64)) < 1e-6
