@@ -182,13 +182,22 @@ def oracle_sample(A_np, b_np, tab, q, alpha_sample, seed, threads):
     return q * alpha_sample, dt
 
 
+def sample_alpha(A_np, b_np, tab, q, seed, threads, target_s):
+    """Projections per worker so that one oracle round takes about target_s:
+    two probes separate the fixed cost of a call (row norms) from the
+    per-projection cost."""
+    _, t1 = oracle_sample(A_np, b_np, tab, q, 10, seed, threads)
+    _, t2 = oracle_sample(A_np, b_np, tab, q, 40, seed, threads)
+    per = max((t2 - t1) / 30.0, 1e-7)
+    fixed = max(t1 - 10 * per, 0.0)
+    return max(10, int((target_s - fixed) / per))
+
+
 def cpu_baseline(A_np, b_np, q, seed, target_s):
     import oracle
     threads = os.cpu_count() or 1
     tab = oracle.table(A_np)
-    probe = 20
-    units, dt = oracle_sample(A_np, b_np, tab, q, probe, seed, threads)
-    alpha_s = max(probe, int(probe * target_s / max(dt, 1e-3)))
+    alpha_s = sample_alpha(A_np, b_np, tab, q, seed, threads, target_s)
     units, dt = oracle_sample(A_np, b_np, tab, q, alpha_s, seed, threads)
     return {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"1 RKAB round of q={q} workers x alpha={alpha_s} projections "
@@ -206,10 +215,8 @@ def run_reference(args):
     s = rk_inputs.gaussian_system(args.m, n, seed=args.seed)
     threads = os.cpu_count() or 1
     tab = oracle.table(s.A)
-    probe = 20
-    _, dt = oracle_sample(s.A, s.b, tab, args.q, probe, args.seed, threads)
     per_step_target = max(1.0, min(20.0, 120.0 / max(args.steps + args.warmup, 1)))
-    alpha_s = max(probe, int(probe * per_step_target / max(dt, 1e-3)))
+    alpha_s = sample_alpha(s.A, s.b, tab, args.q, args.seed, threads, per_step_target)
     for _ in range(args.warmup):
         oracle_sample(s.A, s.b, tab, args.q, alpha_s, args.seed, threads)
     tot_u, tot_t = 0, 0.0

@@ -4,20 +4,27 @@
 //
 // One CTA per worker gamma.  Warp layout of a CTA:
 //   warps 0 .. NT/32-1  consumers: each thread owns VPT float4 slices of the
-//                       worker's iterate v (registers) and, per projection,
-//                       the matching slices of the sampled row;
+//                       round's start point x and of the worker's displacement
+//                       d = v - x (registers) and, per projection, the
+//                       matching slices of the sampled row;
 //   warp NT/32          producer: draws the row indices ahead (they do not
 //                       depend on v), loads b_i and 1/||A_i||^2 and moves each
 //                       row HBM -> shared memory with one bulk asynchronous
 //                       copy into a ring of `stages` buffers (mbarrier
 //                       full/empty handshake).
-// Per projection the consumers compute <A_i, v> (per-thread FMA chain, warp
-// butterfly, fixed-order sum of the warp partials), the scale
-// omega (b_i - <A_i, v>) / ||A_i||^2, and v += scale A_i, with one named
-// barrier.  After `alpha` projections every CTA writes v to row gamma of V,
-// a grid barrier follows, each CTA averages a slice of columns over
-// gamma = 0 .. q-1 in that order into x, a second grid barrier follows, and
-// every CTA reloads x into v.  Every wait is bounded in time.
+// Per projection the consumers compute <A_i, v> = <A_i, x> + <A_i, d>
+// (per-thread FMA chain, warp butterfly, fixed-order sum of the warp
+// partials), the scale omega (b_i - <A_i, v>) / ||A_i||^2, and d += scale A_i,
+// with one named barrier.  After `alpha` projections every CTA writes d to row
+// gamma of V, a grid barrier follows, each CTA forms x + (1/q) sum_gamma d_gamma
+// for a slice of columns, a second grid barrier follows, and every CTA reloads
+// x and clears d.  Every wait is bounded in time.
+//
+// The worker keeps v as x + d, the difference form of Algorithm 3 (v - x is
+// what gets averaged): near convergence a projection changes v_j by far less
+// than half an ulp of v_j, so an iterate stored whole in float32 stops moving
+// (stagnation near 1e-6 relative error on the 80000 x 10000 system); d is small
+// and keeps the updates, and x is rounded once per round.
 #include <algorithm>
 #include <cstdint>
 
@@ -183,13 +190,34 @@ __device__ void producer_loop(const KParams& p, uint8_t* stages, uint64_t* full,
     __syncwarp();
 }
 
-// x <- (1/q) sum_gamma V[gamma] for this CTA's contiguous slice of float4
-// columns.  When the slice is narrower than the CTA, the workers are split into
+// x <- x + (1/q) sum_gamma d_gamma (d_gamma = V[gamma]) for this CTA's
+// contiguous slice of float4 columns; x is read from x0 in the first round and
+// from xbuf afterwards (only the slice's owner reads and writes it here).  When the slice is narrower than the CTA, the workers are split into
 // `groups` contiguous ranges, each summed in ascending gamma by one thread, and
 // the group sums are added in ascending group order: a fixed two-level order,
 // the same on every run.  Writes the average to xbuf (float4) and to x.
+__device__ __forceinline__ float4 load_x_old(const KParams& p, int c, bool first) {
+    if (!first) return ldcg4(p.xbuf + (size_t)c * 4);
+    const int j = c * 4;
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    t.x = p.x0[j];
+    if (j + 1 < p.n) t.y = p.x0[j + 1];
+    if (j + 2 < p.n) t.z = p.x0[j + 2];
+    if (j + 3 < p.n) t.w = p.x0[j + 3];
+    return t;
+}
+
+__device__ __forceinline__ void store_x(const KParams& p, int c, float4 xm) {
+    reinterpret_cast<float4*>(p.xbuf)[c] = xm;
+    const int j = c * 4;
+    p.x[j] = xm.x;
+    if (j + 1 < p.n) p.x[j + 1] = xm.y;
+    if (j + 2 < p.n) p.x[j + 2] = xm.z;
+    if (j + 3 < p.n) p.x[j + 3] = xm.w;
+}
+
 template <int NT>
-__device__ __forceinline__ void average_slice(const KParams& p, float4* avg) {
+__device__ __forceinline__ void average_slice(const KParams& p, float4* avg, bool first) {
     const int tid = threadIdx.x;
     const int n4 = p.n4;
     const int G = gridDim.x;
@@ -207,13 +235,9 @@ __device__ __forceinline__ void average_slice(const KParams& p, float4* avg) {
                 const float4 w = ldcg4(p.V + (size_t)g * (size_t)p.ldv + (size_t)c * 4);
                 acc.x += w.x; acc.y += w.y; acc.z += w.z; acc.w += w.w;
             }
-            const float4 xm = make_float4(acc.x / qf, acc.y / qf, acc.z / qf, acc.w / qf);
-            reinterpret_cast<float4*>(p.xbuf)[c] = xm;
-            const int j = c * 4;
-            p.x[j] = xm.x;
-            if (j + 1 < p.n) p.x[j + 1] = xm.y;
-            if (j + 2 < p.n) p.x[j + 2] = xm.z;
-            if (j + 3 < p.n) p.x[j + 3] = xm.w;
+            const float4 xo = load_x_old(p, c, first);
+            store_x(p, c, make_float4(xo.x + acc.x / qf, xo.y + acc.y / qf, xo.z + acc.z / qf,
+                                      xo.w + acc.w / qf));
         }
         return;
     }
@@ -237,14 +261,10 @@ __device__ __forceinline__ void average_slice(const KParams& p, float4* avg) {
             const float4 w = avg[gg * nc + tid];
             acc.x += w.x; acc.y += w.y; acc.z += w.z; acc.w += w.w;
         }
-        const float4 xm = make_float4(acc.x / qf, acc.y / qf, acc.z / qf, acc.w / qf);
         const int c = c0 + tid;
-        reinterpret_cast<float4*>(p.xbuf)[c] = xm;
-        const int j = c * 4;
-        p.x[j] = xm.x;
-        if (j + 1 < p.n) p.x[j + 1] = xm.y;
-        if (j + 2 < p.n) p.x[j + 2] = xm.z;
-        if (j + 3 < p.n) p.x[j + 3] = xm.w;
+        const float4 xo = load_x_old(p, c, first);
+        store_x(p, c, make_float4(xo.x + acc.x / qf, xo.y + acc.y / qf, xo.z + acc.z / qf,
+                                  xo.w + acc.w / qf));
     }
 }
 
@@ -290,7 +310,8 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
     // ---------------- consumers ----------------
     const int n4 = p.n4;
     const int gamma = blockIdx.x;
-    float4 v[VPT];
+    float4 v[VPT];   // the round's start point x
+    float4 d[VPT];   // the worker's displacement v - x within the round
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
         const int idx = tid + k * NT;
@@ -303,6 +324,7 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
             if (j + 3 < p.n) t.w = __ldg(p.x0 + j + 3);
         }
         v[k] = t;
+        d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
     int s = 0;
@@ -328,9 +350,13 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 part = fmaf(a[k].x, v[k].x, part);
+                part = fmaf(a[k].x, d[k].x, part);
                 part = fmaf(a[k].y, v[k].y, part);
+                part = fmaf(a[k].y, d[k].y, part);
                 part = fmaf(a[k].z, v[k].z, part);
+                part = fmaf(a[k].z, d[k].z, part);
                 part = fmaf(a[k].w, v[k].w, part);
+                part = fmaf(a[k].w, d[k].w, part);
             }
 #pragma unroll
             for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -343,27 +369,27 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
             const float scale = p.omega * (mb.x - dot) * mb.y;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
-                v[k].x = fmaf(scale, a[k].x, v[k].x);
-                v[k].y = fmaf(scale, a[k].y, v[k].y);
-                v[k].z = fmaf(scale, a[k].z, v[k].z);
-                v[k].w = fmaf(scale, a[k].w, v[k].w);
+                d[k].x = fmaf(scale, a[k].x, d[k].x);
+                d[k].y = fmaf(scale, a[k].y, d[k].y);
+                d[k].z = fmaf(scale, a[k].z, d[k].z);
+                d[k].w = fmaf(scale, a[k].w, d[k].w);
             }
             if (++s == p.stages) { s = 0; ph ^= 1u; }
         }
         if (!ok) break;
 
-        // ---- average: x <- (1/q) sum_gamma v_gamma, gamma in ascending order ----
+        // ---- average: x <- x + (1/q) sum_gamma d_gamma ----
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
             const int idx = tid + k * NT;
-            if (idx < n4) reinterpret_cast<float4*>(Vg)[idx] = v[k];
+            if (idx < n4) reinterpret_cast<float4*>(Vg)[idx] = d[k];
         }
         named_bar_sync(1, NT);
         if (tid == 0) ctrl->flag = grid_barrier(&p.info->bar_count, &p.info->bar_gen, gridDim.x,
                                                  status, p.timeout_ns) ? 1 : 0;
         named_bar_sync(1, NT);
         if (!ctrl->flag) { ok = false; break; }
-        average_slice<NT>(p, avg);
+        average_slice<NT>(p, avg, r == 0);
         named_bar_sync(1, NT);
         if (tid == 0) ctrl->flag = grid_barrier(&p.info->bar_count, &p.info->bar_gen, gridDim.x,
                                                  status, p.timeout_ns) ? 1 : 0;
@@ -373,6 +399,7 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
         for (int k = 0; k < VPT; ++k) {
             const int idx = tid + k * NT;
             v[k] = (idx < n4) ? ldcg4(p.xbuf + (size_t)idx * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
 
         // ---- convergence / divergence check (identical in every CTA) ----

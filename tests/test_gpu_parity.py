@@ -47,7 +47,7 @@ def _check_tables(rk, A_np, plan=None):
     thr = t["thr64"].cpu().numpy().view(np.uint64)
     al = t["alias"].cpu().numpy().view(np.uint32)
     assert np.array_equal(K, tab.K)
-    P_ref = np.concatenate([[0], np.cumsum(tab.K[:-1], dtype=np.uint64)]).astype(np.uint64)
+    P_ref = np.concatenate([np.zeros(1, np.uint64), np.cumsum(tab.K[:-1], dtype=np.uint64)])
     assert np.array_equal(P, P_ref)
     assert np.array_equal(thr, tab.thr64)
     assert np.array_equal(al, tab.alias)
