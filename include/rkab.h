@@ -44,6 +44,7 @@ extern "C" {
 #define RK_ECUDA (-6)           /* a CUDA runtime call failed */
 #define RK_EWORKSPACE (-7)      /* workspace smaller than the size query returned */
 #define RK_ESETUP (-8)          /* the plan's device-side setup failed (see rk_plan_status) */
+#define RK_ETOOLARGE (-9)       /* q x n exceeds the fixed scratch of rkab_solve_noalloc */
 
 /* Storage type of the rows the solver streams. */
 typedef enum {
@@ -160,6 +161,38 @@ size_t rk_solve_workspace_bytes(const rk_plan *plan, int q);
 int rkab_solve(const rk_plan *plan, const float *b, const float *x0, float *x, int q,
                int64_t alpha, int64_t rounds, uint64_t seed, const rk_opts *opts,
                void *workspace, size_t ws_bytes, void *stream);
+
+/* Outcome of a solve as rkab_solve_noalloc reports it (same meaning as rk_solve_status). */
+typedef struct {
+    int32_t status;        /* RK_OK, RK_ETIMEOUT, RK_EDIVERGED or RK_ESETUP */
+    int32_t reserved;
+    int64_t rounds_done;   /* rounds completed */
+    double last_metric;    /* criterion value at the last check, -1 if none */
+} rk_solve_result;
+
+/* Bytes of the fixed device scratch array used by rkab_solve_noalloc. */
+#define RK_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* rkab_solve for callers that cannot allocate device memory: a plugin or callback
+ * hosted by another runtime that owns every device allocation and gives it only a
+ * stream, or a real-time loop that forbids allocation after start-up.  The paper has
+ * no counterpart; it is the same solve as rkab_solve (same kernel, same results) with
+ * its scratch -- the run-state header, the q x n worker displacements and the
+ * averaged iterate -- in one file-scope device array of RK_NOALLOC_SCRATCH_BYTES
+ * (8 MiB) instead of a caller workspace, so it allocates nothing.
+ *   plan, b, x0, x, q, alpha, rounds, seed, opts   as for rkab_solve
+ *   result   where the outcome is written when the solve ends (stream-ordered): any
+ *            address cudaMemcpyAsync accepts (device or pinned host); NULL to skip
+ * Returns RK_ETOOLARGE when rk_solve_workspace_bytes(plan, q) exceeds the array
+ * (about (q + 1) * ceil(n / 4) * 16 bytes; q + 1 <= 209 at n = 10000), before any device
+ * work.  Every GPU that loads the library holds the array until the process exits.
+ * The first call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  All calls on a device
+ * share the array and it keeps the last call's contents (each call clears the
+ * run-state header): calls whose work overlaps on the GPU race on it. */
+int rkab_solve_noalloc(const rk_plan *plan, const float *b, const float *x0, float *x, int q,
+                       int64_t alpha, int64_t rounds, uint64_t seed, const rk_opts *opts,
+                       rk_solve_result *result, void *stream);
 
 /* rkab_solve with alpha = 1 (RKA of Algorithm 1, Eq. (rka_uni_weights)). */
 int rka_solve(const rk_plan *plan, const float *b, const float *x0, float *x, int q,

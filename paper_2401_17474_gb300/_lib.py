@@ -20,6 +20,7 @@ RK_EDIVERGED = -5
 RK_ECUDA = -6
 RK_EWORKSPACE = -7
 RK_ESETUP = -8
+RK_ETOOLARGE = -9
 
 RK_F32, RK_BF16, RK_FP8E4M3 = 0, 1, 2
 
@@ -59,6 +60,9 @@ _SIG = {
     "rkab_solve": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_uint64, ctypes.POINTER(RkOpts), _V, ctypes.c_size_t,
                                   _V]),
+    "rkab_solve_noalloc": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_int, ctypes.c_int64,
+                                          ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(RkOpts),
+                                          _V, _V]),
     "rka_solve": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
                                  ctypes.POINTER(RkOpts), _V, ctypes.c_size_t, _V]),
     "rk_solve_status": (ctypes.c_int, [_V, _V, ctypes.POINTER(ctypes.c_int64),

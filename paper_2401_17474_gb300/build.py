@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librkab.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["rk_api.cu", "rk_setup.cu", "rk_solve.cu", "rk_residual.cu"]
+SOURCES = ["rk_api.cu", "rk_setup.cu", "rk_solve.cu", "rk_residual.cu", "rk_noalloc.cu"]
 
 
 def nvcc() -> str:

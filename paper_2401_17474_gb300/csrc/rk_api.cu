@@ -71,10 +71,6 @@ SetupWs setup_ws_carve(void* base, int64_t m) {
 
 using namespace rk;
 
-struct rk_plan {
-    Plan p;
-};
-
 extern "C" {
 
 void rk_opts_default(rk_opts* o) {
@@ -102,6 +98,7 @@ const char* rk_strerror(int code) {
         case RK_ECUDA: return "CUDA runtime error";
         case RK_EWORKSPACE: return "workspace too small";
         case RK_ESETUP: return "plan setup failed on the device (non-finite or all-zero matrix)";
+        case RK_ETOOLARGE: return "q x n exceeds the fixed scratch of the allocation-free solve";
         default: return "unknown error";
     }
 }

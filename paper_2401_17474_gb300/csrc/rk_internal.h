@@ -101,3 +101,8 @@ void count_launch(int k = 1);
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 }  // namespace rk
+
+// The opaque handle of rkab.h: a host-side Plan.
+struct rk_plan {
+    rk::Plan p;
+};
