@@ -72,6 +72,11 @@ typedef struct {
     int same_stream;       /* nonzero: every worker draws worker 0's rows (test hook) [0] */
     int cluster_size;      /* CTAs per worker: 0 = chosen by the library           [0]   */
     double timeout_s;      /* limit of every device-side wait, seconds              [10]  */
+    int lookahead;         /* rows per look-ahead group (1, 2 or 4): the dots of the
+                              next rows and their pairwise products are reduced once
+                              per group and the projections resolved by a scalar
+                              recurrence (same result as one row at a time in exact
+                              arithmetic); 0 = chosen by the library               [0]   */
 } rk_opts;
 
 void rk_opts_default(rk_opts *opts);
@@ -204,6 +209,46 @@ int rka_solve(const rk_plan *plan, const float *b, const float *x0, float *x, in
  * *last_metric (criterion value at the last check, -1 if none) may be NULL. */
 int rk_solve_status(const void *workspace, void *stream, int64_t *rounds_done,
                     double *last_metric);
+
+/* ------------------------------------------------------------------------ */
+/* Precision form: rows stored in BF16 or FP8 e4m3 (per-row float32 scale)   */
+/* halve or quarter the bytes per projection; outer iterative refinement    */
+/* with the float32 master A and float64-accumulated residuals wins back   */
+/* the accuracy.  Not in the paper (whose precision is unstated); the inner */
+/* solves are RKAB (Section 3.4.1) on the stored rows.                       */
+/* ------------------------------------------------------------------------ */
+
+/* Quantise A (device float32, m x n, lda) into out (device, m x ldo elements of dt):
+ *   RK_BF16     out_ij = bf16 round-to-nearest-even of a_ij
+ *   RK_FP8E4M3  s_i = max_j |a_ij| / 448 in float32 (1 for an all-zero row), written to
+ *               row_scale[i] (device, m floats); out_ij = e4m3 round-to-nearest-even of
+ *               a_ij / s_i, saturating to +-448 (OCP finite-only variant)
+ * Columns n .. ldo-1 of out are zeroed.  ldo * element size must be a multiple of 16.
+ * Asynchronous on `stream`. */
+int rk_quantize(const float *A, int64_t m, int64_t n, int64_t lda, rk_dtype dt, void *out,
+                int64_t ldo, float *row_scale, void *stream);
+
+/* Bytes of device workspace rkab_refine needs for the stored-row plan and q workers. */
+size_t rk_refine_workspace_bytes(const rk_plan *lowp, int q);
+
+/* Iterative refinement of Ax = b.  x starts at x0 (may alias x); for outer = 0, 1, ...:
+ *   r = b - A32 x               (float32 master rows, float64 accumulation, rounded to float32)
+ *   d = RKAB on the rows of `lowp` for A~ d = r from d = 0: q workers, alpha projections
+ *       per round, inner_rounds rounds, Philox stream id 3 + (outer << 8), relaxation
+ *       opts->omega
+ *   x = x + d                   (float32)
+ * and stops after max_outer steps or, with opts->criterion = 1, after the first step with
+ * ||x - x_ref|| / ||x_ref|| < opts->tol.  Synchronises `stream` once per outer step to read
+ * the inner solve's status and the criterion; returns RK_OK or the first error (device
+ * status of an inner solve included).  *outer_done and *last_metric (may be NULL) receive
+ * the steps done and the criterion after the last one (-1 without a criterion).
+ *   lowp     plan of the stored copy (RK_BF16, RK_FP8E4M3, or RK_F32 for plain refinement)
+ *   A32      device float32 master rows (m x n, lda32), the same system as lowp's rows
+ *   workspace  device, >= rk_refine_workspace_bytes(lowp, q), 256-byte aligned */
+int rkab_refine(const rk_plan *lowp, const float *A32, int64_t lda32, const float *b,
+                const float *x0, float *x, int q, int64_t alpha, int64_t inner_rounds,
+                int64_t max_outer, uint64_t seed, const rk_opts *opts, void *workspace,
+                size_t ws_bytes, void *stream, int64_t *outer_done, double *last_metric);
 
 /* ------------------------------------------------------------------------ */
 /* Residual of Eq. (system) / Eq. (ls_system) with float32 A and float64     */

@@ -289,6 +289,41 @@ def fp8_row_scales(A):
     return s
 
 
+def quantize_bf16(A):
+    """(uint16 codes, float32 values) of the BF16 copy of A (round-to-nearest-even)."""
+    A = np.ascontiguousarray(A, np.float32)
+    codes = bf16_rne(A).reshape(A.shape)
+    return codes, bf16_values(codes).reshape(A.shape)
+
+
+def quantize_fp8(A):
+    """(uint8 e4m3 codes, float32 row scales, float32 stored values fl32(s_i q_ij)):
+    s_i = amax_i / 448 in float32, q_ij = e4m3 round-to-nearest-even of a_ij / s_i
+    (float32 division), saturating."""
+    A = np.ascontiguousarray(A, np.float32)
+    s = fp8_row_scales(A)
+    ratio = (A / s[:, None]).astype(np.float32)
+    codes = fp8e4m3_rne(ratio).reshape(A.shape)
+    vals = fp8e4m3_values(codes).astype(np.float32)
+    stored = (vals * s[:, None]).astype(np.float32)
+    return codes, s, stored
+
+
+def refine(A32, A_low, b, x0, q, alpha, inner_rounds, outer, seed, tab_low, omega=1.0):
+    """Iterative refinement of A32 x = b: for each outer step o, r = b - A32 x (FP64),
+    d = RKAB on the stored rows A_low for A_low d = r from d = 0 (Philox stream id
+    3 + (o << 8)), x = x + d.  Returns the iterates after each step."""
+    x = np.array(x0, np.float64)
+    xs = []
+    for o in range(outer):
+        r, _, _ = residual(A32, b, x)
+        d = rkab(A_low, r, np.zeros(x.shape[0]), q=q, alpha=alpha, rounds=inner_rounds, seed=seed,
+                 tab=tab_low, stream=3 + (o << 8), omega=omega)
+        x = x + d
+        xs.append(x.copy())
+    return xs
+
+
 # --------------------------------------------------------------------------
 # Least-squares references (library QR, textbook CGLS)
 # --------------------------------------------------------------------------

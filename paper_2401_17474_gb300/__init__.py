@@ -7,15 +7,18 @@ binding's entry points raises if it is missing.  There is no CPU path.
 """
 from .api import (  # noqa: F401
     Plan,
+    Refiner,
     Residual,
     RkError,
     Solver,
     aligned_rows,
     launch_count,
     make_opts,
+    quantize,
     rk_residual,
     rk_sample_indices,
     rk_setup,
     rka_solve,
+    rkab_refine,
     rkab_solve,
 )

@@ -38,6 +38,7 @@ class RkOpts(ctypes.Structure):
         ("same_stream", ctypes.c_int),
         ("cluster_size", ctypes.c_int),
         ("timeout_s", ctypes.c_double),
+        ("lookahead", ctypes.c_int),
     ]
 
 
@@ -67,6 +68,14 @@ _SIG = {
                                  ctypes.POINTER(RkOpts), _V, ctypes.c_size_t, _V]),
     "rk_solve_status": (ctypes.c_int, [_V, _V, ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_double)]),
+    "rk_quantize": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                   ctypes.c_int, _V, ctypes.c_int64, _V, _V]),
+    "rk_refine_workspace_bytes": (ctypes.c_size_t, [_V, ctypes.c_int]),
+    "rkab_refine": (ctypes.c_int, [_V, _V, ctypes.c_int64, _V, _V, _V, ctypes.c_int,
+                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+                                   ctypes.POINTER(RkOpts), _V, ctypes.c_size_t, _V,
+                                   ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_double)]),
     "rk_residual_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     "rk_residual": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _V, _V,
                                    _V, _V, ctypes.c_int, _V, ctypes.c_size_t, _V]),

@@ -141,7 +141,7 @@ class SolveInfo:
 
 
 def make_opts(omega=1.0, check_every=1, tol=0.0, x_ref=None, round0=0, stream_id=0,
-              same_stream=False, cluster_size=0, timeout_s=10.0) -> RkOpts:
+              same_stream=False, cluster_size=0, timeout_s=10.0, lookahead=0) -> RkOpts:
     o = RkOpts()
     _lib.load().rk_opts_default(ctypes.byref(o))
     o.omega = float(omega)
@@ -154,6 +154,7 @@ def make_opts(omega=1.0, check_every=1, tol=0.0, x_ref=None, round0=0, stream_id
     o.same_stream = int(bool(same_stream))
     o.cluster_size = int(cluster_size)
     o.timeout_s = float(timeout_s)
+    o.lookahead = int(lookahead)
     return o
 
 
@@ -191,8 +192,8 @@ def _vec(t, n, name):
 
 def rkab_solve(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, rounds: int = 1,
                seed: int = 0, *, omega=1.0, x_ref=None, tol=0.0, check_every=1, round0=0,
-               stream_id=0, same_stream=False, timeout_s=10.0, out=None, solver=None,
-               stream=None, raise_on_error=True):
+               stream_id=0, same_stream=False, timeout_s=10.0, lookahead=0, out=None,
+               solver=None, stream=None, raise_on_error=True):
     """RKAB solve (alpha projections per worker between averages); returns (x, info)."""
     b = _vec(b, plan.m, "b")
     if x0 is None:
@@ -202,7 +203,8 @@ def rkab_solve(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, rounds: int =
     if x_ref is not None:
         x_ref = _vec(x_ref, plan.n, "x_ref")
     s = solver if solver is not None else Solver(plan, q)
-    opts = make_opts(omega, check_every, tol, x_ref, round0, stream_id, same_stream, 0, timeout_s)
+    opts = make_opts(omega, check_every, tol, x_ref, round0, stream_id, same_stream, 0, timeout_s,
+                     lookahead)
     s.launch(b, x0, x, alpha, rounds, seed, opts, stream)
     info = s.info(stream)
     if raise_on_error and info.status != _lib.RK_OK:
@@ -213,6 +215,69 @@ def rkab_solve(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, rounds: int =
 def rka_solve(plan: Plan, b, x0=None, q: int = 1, rounds: int = 1, seed: int = 0, **kw):
     """RKA (alpha = 1): Eq. (rka_uni_weights)."""
     return rkab_solve(plan, b, x0, q=q, alpha=1, rounds=rounds, seed=seed, **kw)
+
+
+def quantize(A: torch.Tensor, dtype: str, stream=None):
+    """Stored copy of the float32 rows of A: 'bf16' -> (bf16 tensor, None);
+    'fp8' -> (uint8 e4m3 codes, float32 row scales).  Rows padded to 16 bytes."""
+    if dtype not in ("bf16", "fp8"):
+        raise ValueError("dtype must be 'bf16' or 'fp8'")
+    if A.dtype != torch.float32 or A.stride(1) != 1 or not A.is_cuda:
+        raise ValueError("A must be a float32 CUDA matrix with unit column stride")
+    m, n = A.shape
+    per = 16 // _ELEM[dtype]
+    ldo = (n + per - 1) // per * per
+    out = torch.empty((m, ldo), dtype=_TORCH_DT[dtype], device=A.device)
+    scale = torch.empty(m, dtype=torch.float32, device=A.device) if dtype == "fp8" else None
+    check(_lib.load().rk_quantize(_ptr(A), m, n, A.stride(0), _DT[dtype], _ptr(out), ldo,
+                                  _ptr(scale), _stream(stream)), "rk_quantize")
+    return out[:, :n], scale
+
+
+@dataclass
+class RefineInfo:
+    outer_done: int
+    last_metric: float
+
+
+class Refiner:
+    """Reusable workspace for rkab_refine on one stored-row plan and worker count."""
+
+    def __init__(self, lowp: Plan, q: int):
+        self.plan = lowp
+        self.q = int(q)
+        nbytes = _lib.load().rk_refine_workspace_bytes(lowp.handle, self.q)
+        if nbytes == 0:
+            raise RkError(_lib.RK_EINVAL, "rk_refine_workspace_bytes")
+        self.ws = _workspace(nbytes, lowp.device)
+
+    def run(self, A32, b, x0, x, alpha, inner_rounds, max_outer, seed, opts: RkOpts, stream=None):
+        od = ctypes.c_int64()
+        lm = ctypes.c_double()
+        check(_lib.load().rkab_refine(self.plan.handle, _ptr(A32), A32.stride(0), _ptr(b), _ptr(x0),
+                                      _ptr(x), self.q, int(alpha), int(inner_rounds),
+                                      int(max_outer), int(seed), ctypes.byref(opts), _ptr(self.ws),
+                                      self.ws.numel(), _stream(stream), ctypes.byref(od),
+                                      ctypes.byref(lm)), "rkab_refine")
+        return RefineInfo(int(od.value), float(lm.value))
+
+
+def rkab_refine(lowp: Plan, A32: torch.Tensor, b, x0=None, q: int = 1, alpha: int = 1,
+                inner_rounds: int = 1, max_outer: int = 1, seed: int = 0, *, omega=1.0,
+                x_ref=None, tol=0.0, timeout_s=10.0, out=None, refiner=None, stream=None):
+    """Iterative refinement: FP64-accumulated residual on the float32 master A32,
+    RKAB correction on the stored rows of `lowp`; returns (x, RefineInfo)."""
+    b = _vec(b, lowp.m, "b")
+    if x0 is None:
+        x0 = torch.zeros(lowp.n, dtype=torch.float32, device=lowp.device)
+    x0 = _vec(x0, lowp.n, "x0")
+    x = out if out is not None else torch.empty(lowp.n, dtype=torch.float32, device=lowp.device)
+    if x_ref is not None:
+        x_ref = _vec(x_ref, lowp.n, "x_ref")
+    r = refiner if refiner is not None else Refiner(lowp, q)
+    opts = make_opts(omega, 0, tol, x_ref, 0, 0, False, 0, timeout_s)
+    info = r.run(A32, b, x0, x, alpha, inner_rounds, max_outer, seed, opts, stream)
+    return x, info
 
 
 class Residual:

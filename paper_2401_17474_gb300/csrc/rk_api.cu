@@ -85,6 +85,7 @@ void rk_opts_default(rk_opts* o) {
     o->same_stream = 0;
     o->cluster_size = 0;
     o->timeout_s = 10.0;
+    o->lookahead = 0;
 }
 
 const char* rk_strerror(int code) {
@@ -191,7 +192,8 @@ int rkab_solve(const rk_plan* plan, const float* b, const float* x0, float* x, i
     if (opts) o = *opts;
     if (!(o.omega > 0.0f && o.omega < 2.0f) || o.check_every < 0 || o.round0 < 0 ||
         !(o.timeout_s > 0.0) || (o.criterion == 1 && !o.x_ref) || o.criterion < 0 ||
-        o.criterion > 1)
+        o.criterion > 1 || !(o.lookahead == 0 || o.lookahead == 1 || o.lookahead == 2 ||
+                             o.lookahead == 4))
         return RK_EINVAL;
     if (((uintptr_t)workspace & 255u) != 0) return RK_EALIGN;
     if (ws_bytes < solve_ws_bytes(&plan->p, q)) return RK_EWORKSPACE;
@@ -239,6 +241,40 @@ int rk_solve_status(const void* workspace, void* stream, int64_t* rounds_done,
     if (rounds_done) *rounds_done = info.rounds_done;
     if (last_metric) *last_metric = info.last_metric;
     return info.status;
+}
+
+int rk_quantize(const float* A, int64_t m, int64_t n, int64_t lda, rk_dtype dt, void* out,
+                int64_t ldo, float* row_scale, void* stream) {
+    if (!A || !out || m < 1 || n < 1 || lda < n || ldo < n) return RK_EINVAL;
+    if (dt != RK_BF16 && dt != RK_FP8E4M3) return RK_EINVAL;
+    if (dt == RK_FP8E4M3 && !row_scale) return RK_EINVAL;
+    if (!aligned16(out) || ((size_t)ldo * elem_bytes(dt)) % 16 != 0) return RK_EALIGN;
+    return launch_quantize(A, m, n, lda, dt, out, ldo, row_scale, static_cast<cudaStream_t>(stream));
+}
+
+size_t rk_refine_workspace_bytes(const rk_plan* lowp, int q) {
+    if (!lowp || q < 1) return 0;
+    return refine_ws_bytes(&lowp->p, q);
+}
+
+int rkab_refine(const rk_plan* lowp, const float* A32, int64_t lda32, const float* b,
+                const float* x0, float* x, int q, int64_t alpha, int64_t inner_rounds,
+                int64_t max_outer, uint64_t seed, const rk_opts* opts, void* workspace,
+                size_t ws_bytes, void* stream, int64_t* outer_done, double* last_metric) {
+    if (!lowp || !A32 || !b || !x0 || !x || !workspace || q < 1 || alpha < 1 ||
+        inner_rounds < 1 || max_outer < 0 || lda32 < lowp->p.n)
+        return RK_EINVAL;
+    if (!aligned16(A32) || (lda32 * 4) % 16 != 0 || ((uintptr_t)workspace & 255u) != 0)
+        return RK_EALIGN;
+    rk_opts o;
+    rk_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(o.omega > 0.0f && o.omega < 2.0f) || !(o.timeout_s > 0.0) ||
+        (o.criterion == 1 && !o.x_ref) || o.criterion < 0 || o.criterion > 1)
+        return RK_EINVAL;
+    if (ws_bytes < refine_ws_bytes(&lowp->p, q)) return RK_EWORKSPACE;
+    return run_refine(&lowp->p, A32, lda32, b, x0, x, q, alpha, inner_rounds, max_outer, seed, o,
+                      workspace, static_cast<cudaStream_t>(stream), outer_done, last_metric);
 }
 
 size_t rk_residual_workspace_bytes(int64_t m, int64_t n) {

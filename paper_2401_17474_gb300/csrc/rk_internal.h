@@ -96,6 +96,14 @@ int launch_residual(const float* A, int64_t m, int64_t n, int64_t lda, const flo
                     const float* x, double* r, double* norms_out, int want_atr, void* ws,
                     cudaStream_t st);
 
+int launch_quantize(const float* A, int64_t m, int64_t n, int64_t lda, rk_dtype dt, void* out,
+                    int64_t ldo, float* row_scale, cudaStream_t st);
+size_t refine_ws_bytes(const Plan* pl, int q);
+int run_refine(const Plan* lowp, const float* A32, int64_t lda32, const float* b, const float* x0,
+               float* x, int q, int64_t alpha, int64_t inner_rounds, int64_t max_outer,
+               uint64_t seed, const rk_opts& o, void* ws, cudaStream_t st, int64_t* outer_done,
+               double* last_metric);
+
 void count_launch(int k = 1);
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }

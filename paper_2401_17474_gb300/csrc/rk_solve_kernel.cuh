@@ -1,0 +1,768 @@
+// rk_solve_kernel.cuh -- persistent RKAB kernel (Section 3.4.1, Algorithm 3;
+// alpha = 1 is RKA, Algorithm 1 / Eq. (rka_uni_weights); q = 1 is RK,
+// Eq. (alg) with the draws of Eq. (prob_line)), templated on the stored row
+// type (float32, bfloat16, FP8 e4m3 with a per-row scale).  Instantiated in
+// rk_solve_f32.cu, rk_solve_bf16.cu and rk_solve_fp8.cu; launched by rk_solve.cu.
+//
+// One CTA per worker gamma.  Warp layout of a CTA:
+//   warps 0 .. NT/32-1  consumers: each thread owns VPT four-element slices of
+//                       the round's start point x and of the worker's
+//                       displacement d = v - x (registers, float32) and, per
+//                       projection, the matching elements of the sampled row;
+//   warp NT/32          producer: draws the row indices ahead (they do not
+//                       depend on v), loads b_i, 1/||A_i||^2 (and the FP8 row
+//                       scale) and moves each stored row HBM -> shared memory
+//                       with one bulk asynchronous copy into a ring of
+//                       `stages` buffers (mbarrier full/empty handshake).
+// Per projection the consumers compute <A_i, v> = <A_i, x> + <A_i, d>
+// (per-thread FMA chain, warp butterfly, fixed-order sum of the warp
+// partials), the scale omega (b_i - <A_i, v>) / ||A_i||^2, and d += scale A_i,
+// with one named barrier.  Rows stored in BF16 or FP8 are widened to float32
+// in registers; the FP8 row scale s_i multiplies the dot and the update scalar
+// (A_i = s_i q_i), so the arithmetic stays float32.  After `alpha`
+// projections every CTA writes d to row gamma of V, a grid barrier follows,
+// each CTA forms x + (1/q) sum_gamma d_gamma for a slice of columns, a second
+// grid barrier follows, and every CTA reloads x and clears d.  Every wait is
+// bounded in time.
+//
+// The worker keeps v as x + d, the difference form of Algorithm 3 (v - x is
+// what gets averaged): near convergence a projection changes v_j by far less
+// than half an ulp of v_j, so an iterate stored whole in float32 stops moving
+// (stagnation near 1e-6 relative error on the 80000 x 10000 system); d is small
+// and keeps the updates, and x is rounded once per round.
+//
+// KEEP_A: the row's slices stay in registers between the dot and the update
+// (the stage is released right after it is read).  Without it (wide rows, where
+// x, d and the row together would not fit in registers) the update reads the
+// stage a second time and the stage is released after the update.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include <cstdint>
+
+#include "rk_common.cuh"
+#include "rk_internal.h"
+
+namespace rk {
+
+enum { ELT_F32 = 0, ELT_BF16 = 1, ELT_FP8 = 2 };
+
+struct KParams {
+    const uint8_t* A;       // stored rows
+    int64_t lda_bytes;
+    uint64_t m;
+    int n;
+    int n4;                 // ceil(n / 4): four-element slices per row
+    const float* b;
+    const float* inv;
+    const float* row_scale; // FP8 only
+    const uint64_t* thr64;
+    const uint32_t* alias;
+    const float* x0;
+    float* x;
+    float* xbuf;            // n4 float4, the average (workspace)
+    float* V;               // q x ldv
+    int64_t ldv;
+    int q;
+    int64_t alpha;
+    int64_t rounds;
+    int64_t round0;
+    uint64_t seed;
+    uint32_t stream_id;
+    int same_stream;
+    float omega;
+    const float* x_ref;
+    double tol;
+    int64_t check_every;
+    int criterion;
+    SolveInfo* info;
+    const SetupInfo* setup;
+    uint64_t timeout_ns;
+    int stages;
+    uint32_t row_bytes;     // bytes moved per row (multiple of 16)
+    uint32_t stage_stride;  // bytes between stages in shared memory
+};
+
+struct Ctrl {
+    long long stop_t;   // producer issues projections t < stop_t
+    int flag;           // broadcast slot
+    int pad;
+};
+
+__device__ __forceinline__ bool bar_and(int id, int nthreads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity, uint64_t timeout_ns,
+                                            int* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer_ns() - t0 > timeout_ns) {
+            set_status(status, RK_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ float4 ldcg4(const float* p) {
+    return __ldcg(reinterpret_cast<const float4*>(p));
+}
+
+// Zero the elements of the row's last slice that lie beyond column n (they are
+// copied from the row's padding).  rem = n mod 4 (nonzero here).
+__device__ __forceinline__ float4 zero_beyond(float4 v, int rem) {
+    if (rem < 2) v.y = 0.f;
+    if (rem < 3) v.z = 0.f;
+    v.w = 0.f;
+    return v;
+}
+
+template <int ELT>
+__device__ __forceinline__ float4 load4(const uint8_t* stage, int idx) {
+    if constexpr (ELT == ELT_F32) {
+        return reinterpret_cast<const float4*>(stage)[idx];
+    } else if constexpr (ELT == ELT_BF16) {
+        const uint2 w = reinterpret_cast<const uint2*>(stage)[idx];
+        return make_float4(__uint_as_float(w.x << 16), __uint_as_float(w.x & 0xFFFF0000u),
+                           __uint_as_float(w.y << 16), __uint_as_float(w.y & 0xFFFF0000u));
+    } else {
+        const uint32_t w = reinterpret_cast<const uint32_t*>(stage)[idx];
+        const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xFFFFu), __NV_E4M3);
+        const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+        const float2 a = __half22float2(__half2(lo));
+        const float2 c = __half22float2(__half2(hi));
+        return make_float4(a.x, a.y, c.x, c.y);
+    }
+}
+
+// Slice k of this thread as stored in the stage.  Stages are padded to NT*VPT
+// slices and zeroed once when the kernel starts (copies never write beyond the
+// row), so slices past the row read zeros and need no bounds check; only the
+// row's last slice, when n is not a multiple of 4, is masked (tail_k is the k
+// of that slice for the one thread that owns it, -1 elsewhere).
+template <int ELT>
+__device__ __forceinline__ float4 slice(const uint8_t* stg, int idx, int k, int tail_k, int rem) {
+    float4 a = load4<ELT>(stg, idx);
+    if (k == tail_k) a = zero_beyond(a, rem);
+    return a;
+}
+
+// Four stored elements of slice idx of a stage, widened to float32 (the FP8 row
+// scale is not applied here).
+template <int ELT>
+__device__ void producer_loop(const KParams& p, uint8_t* stages, uint64_t* full, uint64_t* empty,
+                              float4* meta, volatile Ctrl* ctrl, float4* pbuf) {
+    const int lane = threadIdx.x & 31;
+    const int S = p.stages;
+    const int64_t total = p.rounds * p.alpha;
+    const uint32_t worker = p.same_stream ? 0u : (uint32_t)blockIdx.x;
+    const uint64_t tbase = (uint64_t)p.round0 * (uint64_t)p.alpha;
+    const uint64_t pol = policy_evict_first();
+    int* status = &p.info->status;
+    int64_t issued = 0;
+    int s = 0;
+    uint32_t pass = 0;      // parity of the current pass over the ring of stages
+    bool stop = false;
+    for (int64_t base = 0; base < total && !stop; base += 32) {
+        // the warp draws 32 rows at once (their indices do not depend on v) ...
+        const int64_t tl = base + lane;
+        if (tl < total) {
+            const uint32_t row = sample_row(p.seed, worker, p.stream_id, tbase + (uint64_t)tl, p.m,
+                                            p.thr64, p.alias);
+            const float sc = (ELT == ELT_FP8) ? __ldg(p.row_scale + row) : 1.f;
+            pbuf[lane] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row), sc);
+        }
+        __syncwarp();
+        // ... and one lane moves them, in order, into the ring of stages
+        if (lane == 0) {
+            const int64_t rem_ = total - base;
+            const int cnt = rem_ < 32 ? (int)rem_ : 32;
+            for (int k = 0; k < cnt && !stop; ++k) {
+                const int64_t tt = base + k;
+                if (tt >= ctrl->stop_t) {
+                    stop = true;
+                    break;
+                }
+                if (tt >= S) {
+                    // wait until the consumers released this stage's row of the
+                    // previous pass (phase parity = previous pass parity)
+                    const uint32_t prev = pass ^ 1u;
+                    if (!mbar_try_wait(&empty[s], prev)) {
+                        const uint64_t t0 = globaltimer_ns();
+                        while (!mbar_try_wait(&empty[s], prev)) {
+                            if (tt >= ctrl->stop_t) { stop = true; break; }
+                            if (globaltimer_ns() - t0 > p.timeout_ns) {
+                                set_status(status, RK_ETIMEOUT);
+                                stop = true;
+                                break;
+                            }
+                        }
+                    }
+                    if (stop) break;
+                }
+                const float4 e = pbuf[k];
+                const uint32_t row = __float_as_uint(e.x);
+                meta[s] = make_float4(e.y, e.z, e.w, 0.f);
+                mbar_arrive_expect_tx(&full[s], p.row_bytes);
+                bulk_g2s(stages + (size_t)s * p.stage_stride, p.A + (size_t)row * (size_t)p.lda_bytes,
+                         p.row_bytes, &full[s], pol);
+                issued = tt + 1;
+                if (++s == S) { s = 0; pass ^= 1u; }
+            }
+        }
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        __syncwarp();
+    }
+    // Drain: every copy this warp issued must have landed before the CTA exits.
+    if (lane == 0) {
+        const int64_t first = issued > S ? issued - S : 0;
+        for (int64_t tt = first; tt < issued; ++tt) {
+            const int st = (int)(tt % S);
+            const uint32_t par = (uint32_t)((tt / S) & 1);
+            wait_parity(&full[st], par, p.timeout_ns, status);
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ float4 load_x_old(const KParams& p, int c, bool first) {
+    if (!first) return ldcg4(p.xbuf + (size_t)c * 4);
+    const int j = c * 4;
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    t.x = p.x0[j];
+    if (j + 1 < p.n) t.y = p.x0[j + 1];
+    if (j + 2 < p.n) t.z = p.x0[j + 2];
+    if (j + 3 < p.n) t.w = p.x0[j + 3];
+    return t;
+}
+
+__device__ __forceinline__ void store_x(const KParams& p, int c, float4 xm) {
+    reinterpret_cast<float4*>(p.xbuf)[c] = xm;
+    const int j = c * 4;
+    p.x[j] = xm.x;
+    if (j + 1 < p.n) p.x[j + 1] = xm.y;
+    if (j + 2 < p.n) p.x[j + 2] = xm.z;
+    if (j + 3 < p.n) p.x[j + 3] = xm.w;
+}
+
+// x <- x + (1/q) sum_gamma d_gamma (d_gamma = V[gamma]) for this CTA's
+// contiguous slice of float4 columns; x is read from x0 in the first round and
+// from xbuf afterwards (only the slice's owner reads and writes it here).
+// When the slice is narrower than the CTA, the workers are split into
+// `groups` contiguous ranges, each summed in ascending gamma by one thread, and
+// the group sums are added in ascending group order: a fixed two-level order,
+// the same on every run.
+template <int NT>
+__device__ __forceinline__ void average_slice(const KParams& p, float4* avg, bool first) {
+    const int tid = threadIdx.x;
+    const int n4 = p.n4;
+    const int G = gridDim.x;
+    const int cols = (n4 + G - 1) / G;
+    const int c0 = blockIdx.x * cols;
+    const int c1 = min(n4, c0 + cols);
+    const int nc = c1 - c0;
+    const float qf = (float)p.q;
+    if (nc <= 0) return;
+    if (nc >= NT) {
+        for (int c = c0 + tid; c < c1; c += NT) {
+            float4 acc = ldcg4(p.V + (size_t)c * 4);
+#pragma unroll 8
+            for (int g = 1; g < p.q; ++g) {
+                const float4 w = ldcg4(p.V + (size_t)g * (size_t)p.ldv + (size_t)c * 4);
+                acc.x += w.x; acc.y += w.y; acc.z += w.z; acc.w += w.w;
+            }
+            const float4 xo = load_x_old(p, c, first);
+            store_x(p, c, make_float4(xo.x + acc.x / qf, xo.y + acc.y / qf, xo.z + acc.z / qf,
+                                      xo.w + acc.w / qf));
+        }
+        return;
+    }
+    int groups = NT / nc;
+    if (groups > p.q) groups = p.q;
+    const int per = (p.q + groups - 1) / groups;
+    const int cl = tid % nc, g = tid / nc;
+    if (g < groups) {
+        const int ga = g * per, gb = min(p.q, ga + per);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int gg = ga; gg < gb; ++gg) {
+            const float4 w = ldcg4(p.V + (size_t)gg * (size_t)p.ldv + (size_t)(c0 + cl) * 4);
+            acc.x += w.x; acc.y += w.y; acc.z += w.z; acc.w += w.w;
+        }
+        avg[g * nc + cl] = acc;
+    }
+    named_bar_sync(1, NT);
+    if (tid < nc) {
+        float4 acc = avg[tid];
+        for (int gg = 1; gg < groups; ++gg) {
+            const float4 w = avg[gg * nc + tid];
+            acc.x += w.x; acc.y += w.y; acc.z += w.z; acc.w += w.w;
+        }
+        const int c = c0 + tid;
+        const float4 xo = load_x_old(p, c, first);
+        store_x(p, c, make_float4(xo.x + acc.x / qf, xo.y + acc.y / qf, xo.z + acc.z / qf,
+                                  xo.w + acc.w / qf));
+    }
+}
+
+// Shared memory after the stages: avg[NT] float4, full[S] + empty[S] mbarriers,
+// meta[S] float4, red[2][16][32] float (warp partials, double-buffered), chk[96]
+// double, pbuf[32] float4 (the producer's batch of draws), Ctrl.
+constexpr int kRedSlots = 16;   // partial sums reduced per group of rows (W + W(W-1)/2)
+__host__ __device__ inline size_t solve_ctrl_bytes(int S, int nt) {
+    return (size_t)nt * 16 + (size_t)S * 32 + 2 * kRedSlots * 32 * 4 + 96 * 8 + 32 * 16 + 64;
+}
+
+// Rows of one look-ahead group (W > 1): the consumers take W consecutive rows
+// q_0 .. q_{W-1} of their stream (stored values; A_r = s_r q_r with s_r the FP8
+// row scale, 1 otherwise) and, from the same v = x + d, form in one pass
+//   g_r = <q_r, v>   and   G_rl = <q_r, q_l>  (l < r),
+// reduce these W + W(W-1)/2 sums across the CTA once, then resolve the
+// coefficients of the sequential projections with the scalar recurrence
+//   h_r = g_r + sum_{l<r} c_l G_rl   (= <q_r, v after projections 0 .. r-1>)
+//   c_r = omega (b_r - s_r h_r) / ||A_r||^2 * s_r,
+// and apply d += sum_r c_r q_r.  In exact arithmetic this is the same as W
+// projections of Eq. (alg) one after the other; it pays the CTA-wide reduction
+// once per W rows instead of once per row.
+template <int W>
+struct GroupIdx {
+    static constexpr int NV = W + W * (W - 1) / 2;
+    __device__ static constexpr int gram(int r, int l) { return W + r * (r - 1) / 2 + l; }
+};
+
+template <int NT, int VPT, int ELT, bool KEEP_A, int W>
+__global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
+    static_assert(W == 1 || !KEEP_A, "look-ahead groups re-read their rows");
+    static_assert(GroupIdx<W>::NV <= kRedSlots, "too many partial sums per group");
+    extern __shared__ __align__(128) uint8_t smem[];
+    constexpr int NW = NT / 32;
+    const int S = p.stages;
+    uint8_t* stages = smem;
+    float4* avg = reinterpret_cast<float4*>(smem + (size_t)S * p.stage_stride);  // [NT]
+    uint64_t* full = reinterpret_cast<uint64_t*>(avg + NT);
+    uint64_t* empty = full + S;
+    float4* meta = reinterpret_cast<float4*>(empty + S);
+    float* red = reinterpret_cast<float*>(meta + S);          // [2][kRedSlots][32] partials
+    double* chk = reinterpret_cast<double*>(red + 2 * kRedSlots * 32);  // [3][32] check partials
+    float4* pbuf = reinterpret_cast<float4*>(chk + 96);                  // [32] producer batch
+    volatile Ctrl* ctrl = reinterpret_cast<volatile Ctrl*>(pbuf + 32);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int64_t total = p.rounds * p.alpha;
+    int* status = &p.info->status;
+
+    {
+        uint4* z = reinterpret_cast<uint4*>(stages);
+        const size_t nz = (size_t)S * p.stage_stride / 16;
+        for (size_t i = tid; i < nz; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // the zeros must be visible to the bulk copies' async proxy before any copy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NW);
+        }
+        ctrl->stop_t = total;
+        ctrl->flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (p.setup->status != 0) {
+        if (tid == 0) set_status(status, RK_ESETUP);
+        return;
+    }
+    if (warp == NW) {
+        producer_loop<ELT>(p, stages, full, empty, meta, ctrl, pbuf);
+        return;
+    }
+
+    // ---------------- consumers ----------------
+    const int n4 = p.n4;
+    const int gamma = blockIdx.x;
+    float4 v[VPT];   // the round's start point x
+    float4 d[VPT];   // the worker's displacement v - x within the round
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+        const int idx = tid + k * NT;
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < n4) {
+            const int j = idx * 4;
+            t.x = __ldg(p.x0 + j);
+            if (j + 1 < p.n) t.y = __ldg(p.x0 + j + 1);
+            if (j + 2 < p.n) t.z = __ldg(p.x0 + j + 2);
+            if (j + 3 < p.n) t.w = __ldg(p.x0 + j + 3);
+        }
+        v[k] = t;
+        d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+
+    const int rem = p.n & 3;
+    int tail_k = -1;
+    if (rem && ((n4 - 1 - tid) % NT) == 0 && n4 - 1 >= tid) tail_k = (n4 - 1 - tid) / NT;
+    int s = 0;
+    uint32_t ph = 0;
+    int rp = 0;
+    int64_t t = 0;
+    bool ok = true;
+    float* Vg = p.V + (size_t)gamma * (size_t)p.ldv;
+    for (int64_t r = 0; r < p.rounds && ok; ++r) {
+      if constexpr (W > 1) {
+        constexpr int NV = GroupIdx<W>::NV;
+        for (int64_t j = 0; j < p.alpha; j += W) {
+            const int wc = (p.alpha - j) < W ? (int)(p.alpha - j) : W;
+            int sg[W];
+            uint32_t pg[W];
+            bool got = true;
+#pragma unroll
+            for (int rr = 0; rr < W; ++rr) {
+                const int sr = s + rr;
+                sg[rr] = sr >= p.stages ? sr - p.stages : sr;
+                pg[rr] = sr >= p.stages ? (ph ^ 1u) : ph;
+                if (rr < wc) got = wait_parity(&full[sg[rr]], pg[rr], p.timeout_ns, status) && got;
+            }
+            float acc[NV];
+#pragma unroll
+            for (int u = 0; u < NV; ++u) acc[u] = 0.f;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int idx = tid + k * NT;
+                float4 aq[W];
+#pragma unroll
+                for (int rr = 0; rr < W; ++rr) {
+                    aq[rr] = rr < wc ? slice<ELT>(stages + (size_t)sg[rr] * p.stage_stride, idx, k, tail_k, rem)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int rr = 0; rr < W; ++rr) {
+                    float g = acc[rr];
+                    g = fmaf(aq[rr].x, v[k].x, g);
+                    g = fmaf(aq[rr].y, v[k].y, g);
+                    g = fmaf(aq[rr].z, v[k].z, g);
+                    g = fmaf(aq[rr].w, v[k].w, g);
+                    g = fmaf(aq[rr].x, d[k].x, g);
+                    g = fmaf(aq[rr].y, d[k].y, g);
+                    g = fmaf(aq[rr].z, d[k].z, g);
+                    g = fmaf(aq[rr].w, d[k].w, g);
+                    acc[rr] = g;
+#pragma unroll
+                    for (int ll = 0; ll < rr; ++ll) {
+                        float h = acc[GroupIdx<W>::gram(rr, ll)];
+                        h = fmaf(aq[rr].x, aq[ll].x, h);
+                        h = fmaf(aq[rr].y, aq[ll].y, h);
+                        h = fmaf(aq[rr].z, aq[ll].z, h);
+                        h = fmaf(aq[rr].w, aq[ll].w, h);
+                        acc[GroupIdx<W>::gram(rr, ll)] = h;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < NV; ++u) {
+#pragma unroll
+                for (int o = 16; o; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int u = 0; u < NV; ++u) red[(rp * kRedSlots + u) * 32 + warp] = acc[u];
+            }
+            if (!bar_and(1, NT, got)) { ok = false; break; }
+            float tot[NV];
+#pragma unroll
+            for (int u = 0; u < NV; ++u) {
+                float x_ = lane < NW ? red[(rp * kRedSlots + u) * 32 + lane] : 0.f;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    if (o < NW) x_ += __shfl_xor_sync(0xffffffffu, x_, o);
+                }
+                tot[u] = __shfl_sync(0xffffffffu, x_, 0);
+            }
+            rp ^= 1;
+            float c[W];
+#pragma unroll
+            for (int rr = 0; rr < W; ++rr) {
+                c[rr] = 0.f;
+                if (rr < wc) {
+                    float h = tot[rr];
+#pragma unroll
+                    for (int ll = 0; ll < rr; ++ll) h = fmaf(c[ll], tot[GroupIdx<W>::gram(rr, ll)], h);
+                    const float4 mb = meta[sg[rr]];   // b_r, 1/||A_r||^2, row scale s_r
+                    c[rr] = p.omega * (mb.x - mb.z * h) * mb.y * mb.z;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int idx = tid + k * NT;
+#pragma unroll
+                for (int rr = 0; rr < W; ++rr) {
+                    if (rr < wc) {
+                        const float4 aq = slice<ELT>(stages + (size_t)sg[rr] * p.stage_stride, idx, k, tail_k, rem);
+                        d[k].x = fmaf(c[rr], aq.x, d[k].x);
+                        d[k].y = fmaf(c[rr], aq.y, d[k].y);
+                        d[k].z = fmaf(c[rr], aq.z, d[k].z);
+                        d[k].w = fmaf(c[rr], aq.w, d[k].w);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+#pragma unroll
+                for (int rr = 0; rr < W; ++rr) {
+                    if (rr < wc) mbar_arrive(&empty[sg[rr]]);
+                }
+            }
+            s += wc;
+            if (s >= p.stages) { s -= p.stages; ph ^= 1u; }
+            t += wc;
+        }
+      } else if constexpr (KEEP_A) {
+        // One pass over the slices per row: the update of row t-1 (kept in
+        // registers with its coefficient) is applied in the pass that forms the
+        // dot of row t, then row t replaces it; the last update of the round is
+        // applied before the average.
+        float4 a[VPT];
+        float cprev = 0.f;
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) a[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t j = 0; j < p.alpha; ++j, ++t) {
+            const bool got = wait_parity(&full[s], ph, p.timeout_ns, status);
+            const uint8_t* stg = stages + (size_t)s * p.stage_stride;
+            const float4 mb = meta[s];   // b_i, 1/||A_i||^2, row scale
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#define RK_FUSED_SLICE(LOADEXPR)                                          \
+            {                                                             \
+                const float4 ak = LOADEXPR;                               \
+                d[k].x = fmaf(cprev, a[k].x, d[k].x);                     \
+                d[k].y = fmaf(cprev, a[k].y, d[k].y);                     \
+                d[k].z = fmaf(cprev, a[k].z, d[k].z);                     \
+                d[k].w = fmaf(cprev, a[k].w, d[k].w);                     \
+                p0 = fmaf(ak.x, v[k].x, p0);                              \
+                p1 = fmaf(ak.y, v[k].y, p1);                              \
+                p2 = fmaf(ak.z, v[k].z, p2);                              \
+                p3 = fmaf(ak.w, v[k].w, p3);                              \
+                p0 = fmaf(ak.x, d[k].x, p0);                              \
+                p1 = fmaf(ak.y, d[k].y, p1);                              \
+                p2 = fmaf(ak.z, d[k].z, p2);                              \
+                p3 = fmaf(ak.w, d[k].w, p3);                              \
+                a[k] = ak;                                                \
+            }
+            if (rem == 0) {
+#pragma unroll
+                for (int k = 0; k < VPT; ++k) RK_FUSED_SLICE(load4<ELT>(stg, tid + k * NT))
+            } else {
+#pragma unroll
+                for (int k = 0; k < VPT; ++k) RK_FUSED_SLICE(slice<ELT>(stg, tid + k * NT, k, tail_k, rem))
+            }
+#undef RK_FUSED_SLICE
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            float part = (p0 + p1) + (p2 + p3);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) red[rp * kRedSlots * 32 + warp] = part;
+            if (!bar_and(1, NT, got)) { ok = false; break; }
+            // every warp sums the NW warp partials with the same butterfly, so all
+            // threads of the CTA hold the same dot
+            float dot = lane < NW ? red[rp * kRedSlots * 32 + lane] : 0.f;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                if (o < NW) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            }
+            dot = __shfl_sync(0xffffffffu, dot, 0);
+            rp ^= 1;
+            // A_i = s_i q_i: <A_i, v> = s_i <q_i, v>, d += (scale s_i) q_i
+            cprev = p.omega * (mb.x - mb.z * dot) * mb.y * mb.z;
+            if (++s == p.stages) { s = 0; ph ^= 1u; }
+        }
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            d[k].x = fmaf(cprev, a[k].x, d[k].x);
+            d[k].y = fmaf(cprev, a[k].y, d[k].y);
+            d[k].z = fmaf(cprev, a[k].z, d[k].z);
+            d[k].w = fmaf(cprev, a[k].w, d[k].w);
+        }
+      } else {
+        for (int64_t j = 0; j < p.alpha; ++j, ++t) {
+            const bool got = wait_parity(&full[s], ph, p.timeout_ns, status);
+            const uint8_t* stg = stages + (size_t)s * p.stage_stride;
+            const float4 mb = meta[s];   // b_i, 1/||A_i||^2, row scale
+            // four independent accumulators (one per element of a slice) keep the
+            // FMA pipe fed; they are combined in a fixed order
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+            float4 a[KEEP_A ? VPT : 1];
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int idx = tid + k * NT;
+                const float4 ak = slice<ELT>(stg, idx, k, tail_k, rem);
+                if constexpr (KEEP_A) a[k] = ak;
+                p0 = fmaf(ak.x, v[k].x, p0);
+                p1 = fmaf(ak.y, v[k].y, p1);
+                p2 = fmaf(ak.z, v[k].z, p2);
+                p3 = fmaf(ak.w, v[k].w, p3);
+                p0 = fmaf(ak.x, d[k].x, p0);
+                p1 = fmaf(ak.y, d[k].y, p1);
+                p2 = fmaf(ak.z, d[k].z, p2);
+                p3 = fmaf(ak.w, d[k].w, p3);
+            }
+            if constexpr (KEEP_A) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+            float part = (p0 + p1) + (p2 + p3);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) red[rp * kRedSlots * 32 + warp] = part;
+            if (!bar_and(1, NT, got)) { ok = false; break; }
+            // every warp sums the NW warp partials with the same butterfly, so all
+            // threads of the CTA hold the same dot
+            float dot = lane < NW ? red[rp * kRedSlots * 32 + lane] : 0.f;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                if (o < NW) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            }
+            dot = __shfl_sync(0xffffffffu, dot, 0);
+            rp ^= 1;
+            // A_i = s_i q_i: <A_i, v> = s_i <q_i, v>, d += (scale s_i) q_i
+            const float scale = p.omega * (mb.x - mb.z * dot) * mb.y * mb.z;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                float4 ak;
+                if constexpr (KEEP_A) {
+                    ak = a[k];
+                } else {
+                    const int idx = tid + k * NT;
+                    ak = slice<ELT>(stg, idx, k, tail_k, rem);
+                }
+                d[k].x = fmaf(scale, ak.x, d[k].x);
+                d[k].y = fmaf(scale, ak.y, d[k].y);
+                d[k].z = fmaf(scale, ak.z, d[k].z);
+                d[k].w = fmaf(scale, ak.w, d[k].w);
+            }
+            if constexpr (!KEEP_A) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+            if (++s == p.stages) { s = 0; ph ^= 1u; }
+        }
+      }
+        if (!ok) break;
+
+        // ---- average: x <- x + (1/q) sum_gamma d_gamma ----
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            const int idx = tid + k * NT;
+            if (idx < n4) reinterpret_cast<float4*>(Vg)[idx] = d[k];
+        }
+        named_bar_sync(1, NT);
+        if (tid == 0) ctrl->flag = grid_barrier(&p.info->bar_count, &p.info->bar_gen, gridDim.x,
+                                                 status, p.timeout_ns) ? 1 : 0;
+        named_bar_sync(1, NT);
+        if (!ctrl->flag) { ok = false; break; }
+        average_slice<NT>(p, avg, r == 0);
+        named_bar_sync(1, NT);
+        if (tid == 0) ctrl->flag = grid_barrier(&p.info->bar_count, &p.info->bar_gen, gridDim.x,
+                                                 status, p.timeout_ns) ? 1 : 0;
+        named_bar_sync(1, NT);
+        if (!ctrl->flag) { ok = false; break; }
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            const int idx = tid + k * NT;
+            v[k] = (idx < n4) ? ldcg4(p.xbuf + (size_t)idx * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+
+        // ---- convergence / divergence check (identical in every CTA) ----
+        const int64_t done = r + 1;
+        const bool last = (done == p.rounds);
+        if (p.check_every > 0 && (done % p.check_every == 0 || last)) {
+            float e2 = 0.f, r2 = 0.f, xx = 0.f;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int idx = tid + k * NT;
+                if (idx < n4) {
+                    xx = fmaf(v[k].x, v[k].x, xx);
+                    xx = fmaf(v[k].y, v[k].y, xx);
+                    xx = fmaf(v[k].z, v[k].z, xx);
+                    xx = fmaf(v[k].w, v[k].w, xx);
+                    if (p.criterion == 1) {
+                        const int j0 = idx * 4;
+                        const float vv[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            if (j0 + c < p.n) {
+                                const float xr = __ldg(p.x_ref + j0 + c);
+                                const float dd = vv[c] - xr;
+                                e2 = fmaf(dd, dd, e2);
+                                r2 = fmaf(xr, xr, r2);
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+                r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+                xx += __shfl_xor_sync(0xffffffffu, xx, o);
+            }
+            if (lane == 0) {
+                chk[warp] = (double)e2;
+                chk[32 + warp] = (double)r2;
+                chk[64 + warp] = (double)xx;
+            }
+            named_bar_sync(1, NT);
+            double E2 = 0.0, R2 = 0.0, XX = 0.0;
+            for (int w = 0; w < NW; ++w) {
+                E2 += chk[w];
+                R2 += chk[32 + w];
+                XX += chk[64 + w];
+            }
+            named_bar_sync(1, NT);
+            double metric = -1.0;
+            if (p.criterion == 1) metric = (R2 > 0.0) ? sqrt(E2 / R2) : sqrt(E2);
+            const bool diverged = !isfinite(XX) || (p.criterion == 1 && !isfinite(metric));
+            if (gamma == 0 && tid == 0) {
+                p.info->rounds_done = done;
+                p.info->last_metric = metric;
+            }
+            if (diverged) {
+                if (tid == 0) set_status(status, RK_EDIVERGED);
+                ok = false;
+            } else if (p.criterion == 1 && p.tol > 0.0 && metric < p.tol) {
+                break;  // converged: identical decision in every CTA
+            }
+        } else if (gamma == 0 && tid == 0) {
+            p.info->rounds_done = done;
+        }
+    }
+    // Stop the producer at what was consumed (no-op after the last round).
+    if (tid == 0) ctrl->stop_t = t;
+}
+
+typedef void (*SolveKernelFn)(const KParams);
+
+struct SolveVariant {
+    int nt, vpt;
+    bool keep_a;
+    int w;              // rows per look-ahead group
+    SolveKernelFn fn;
+};
+
+// Instantiation tables (one translation unit per stored type).
+const SolveVariant* solve_variants_f32(int* count);
+const SolveVariant* solve_variants_bf16(int* count);
+const SolveVariant* solve_variants_fp8(int* count);
+
+}  // namespace rk

@@ -147,6 +147,24 @@ def test_rkab_matches_oracle(rk, m, n, q, alpha, rounds, omega):
     assert _rel(x.cpu().numpy(), xo) < TOL
 
 
+@pytest.mark.parametrize("lookahead", [1, 2, 4])
+@pytest.mark.parametrize("m,n,q,alpha,rounds", [(3000, 600, 4, 37, 5), (6000, 2600, 5, 30, 3),
+                                                (8000, 9000, 3, 21, 2)])
+def test_lookahead_groups_match_oracle(rk, lookahead, m, n, q, alpha, rounds):
+    """Rows resolved in groups (one CTA reduction per group, scalar recurrence)
+    follow the same trajectory as one row at a time (alpha not a multiple of
+    the group size: the last group of each round is short)."""
+    s = rk_inputs.gaussian_system(m, n, seed=m + n + 1)
+    plan = rk.rk_setup(_padded(s.A, rk))
+    tab = oracle.table(s.A)
+    x, info = rk.rkab_solve(plan, _dev(s.b), q=q, alpha=alpha, rounds=rounds, seed=13,
+                            lookahead=lookahead)
+    assert info.status == 0
+    xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(n), q=q, alpha=alpha, rounds=rounds,
+                     seed=13, tab=tab)
+    assert _rel(x.cpu().numpy(), xo) < TOL
+
+
 def test_special_cases_on_gpu(rk, c1):
     s, plan, tab, b = c1
     # q = 1 RKAB with alpha = 30 is RK over 30 * rounds projections
