@@ -70,9 +70,12 @@ typedef struct {
     uint32_t stream_id;    /* Philox stream id of the draws: 0 rows of A, 1 rows of
                               A^T, 2 recovery solve, 3 + (outer << 8) refinement    [0]   */
     int same_stream;       /* nonzero: every worker draws worker 0's rows (test hook) [0] */
-    int cluster_size;      /* CTAs per worker: 0 = chosen by the library           [0]   */
+    int cluster_size;      /* CTAs per worker (1, 2, 4, 8, 16): a worker's row is split
+                              into that many column chunks, one per CTA of a thread-
+                              block cluster, reduced through distributed shared
+                              memory; 0 or 1 = one CTA per worker                  [0]   */
     double timeout_s;      /* limit of every device-side wait, seconds              [10]  */
-    int lookahead;         /* rows per look-ahead group (1, 2 or 4): the dots of the
+    int lookahead;         /* rows per look-ahead group (1, 2, 4; 6 with clusters): the dots of the
                               next rows and their pairwise products are reduced once
                               per group and the projections resolved by a scalar
                               recurrence (same result as one row at a time in exact

@@ -192,8 +192,8 @@ def _vec(t, n, name):
 
 def rkab_solve(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, rounds: int = 1,
                seed: int = 0, *, omega=1.0, x_ref=None, tol=0.0, check_every=1, round0=0,
-               stream_id=0, same_stream=False, timeout_s=10.0, lookahead=0, out=None,
-               solver=None, stream=None, raise_on_error=True):
+               stream_id=0, same_stream=False, timeout_s=10.0, lookahead=0, cluster_size=0,
+               out=None, solver=None, stream=None, raise_on_error=True):
     """RKAB solve (alpha projections per worker between averages); returns (x, info)."""
     b = _vec(b, plan.m, "b")
     if x0 is None:
@@ -203,8 +203,8 @@ def rkab_solve(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, rounds: int =
     if x_ref is not None:
         x_ref = _vec(x_ref, plan.n, "x_ref")
     s = solver if solver is not None else Solver(plan, q)
-    opts = make_opts(omega, check_every, tol, x_ref, round0, stream_id, same_stream, 0, timeout_s,
-                     lookahead)
+    opts = make_opts(omega, check_every, tol, x_ref, round0, stream_id, same_stream, cluster_size,
+                     timeout_s, lookahead)
     s.launch(b, x0, x, alpha, rounds, seed, opts, stream)
     info = s.info(stream)
     if raise_on_error and info.status != _lib.RK_OK:

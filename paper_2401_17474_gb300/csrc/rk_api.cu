@@ -193,7 +193,8 @@ int rkab_solve(const rk_plan* plan, const float* b, const float* x0, float* x, i
     if (!(o.omega > 0.0f && o.omega < 2.0f) || o.check_every < 0 || o.round0 < 0 ||
         !(o.timeout_s > 0.0) || (o.criterion == 1 && !o.x_ref) || o.criterion < 0 ||
         o.criterion > 1 || !(o.lookahead == 0 || o.lookahead == 1 || o.lookahead == 2 ||
-                             o.lookahead == 4))
+                             o.lookahead == 4 || o.lookahead == 6) ||
+        o.cluster_size < 0 || o.cluster_size > 16 || (o.cluster_size & (o.cluster_size - 1)) != 0)
         return RK_EINVAL;
     if (((uintptr_t)workspace & 255u) != 0) return RK_EALIGN;
     if (ws_bytes < solve_ws_bytes(&plan->p, q)) return RK_EWORKSPACE;

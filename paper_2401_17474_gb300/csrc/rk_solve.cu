@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "rk_cluster_kernel.cuh"
 #include "rk_solve_kernel.cuh"
 
 namespace rk {
@@ -51,6 +52,76 @@ static int stages_for(uint32_t stride, int nt, int smem_max) {
            (size_t)(S + 1) * stride + solve_ctrl_bytes(S + 1, nt) <= (size_t)smem_max)
         ++S;
     return S;
+}
+
+// Cluster path: each worker is a cluster of C CTAs splitting the row's columns.
+static int launch_cluster_solve(const SolveArgs& a, const KParams& base, int C, cudaStream_t st,
+                                int smem_max) {
+    const Plan* pl = a.plan;
+    const int n4 = base.n4;
+    const uint32_t eb = (uint32_t)elem_size(pl->dt);
+    const int chunk = ((n4 + C - 1) / C + 3) / 4 * 4;
+    if ((C - 1) * chunk >= n4) return RK_EINVAL;   // every CTA must own part of the row
+    int count = 0;
+    const ClusterVariant* tab = pl->dt == RK_F32 ? cluster_variants_f32(&count)
+                              : pl->dt == RK_BF16 ? cluster_variants_bf16(&count)
+                                                  : cluster_variants_fp8(&count);
+    const int nt = 128;
+    const int need = (chunk + nt - 1) / nt;
+    int want_w = a.opts.lookahead > 1 ? a.opts.lookahead : 6;
+    const ClusterVariant* var = nullptr;
+    uint32_t stride = 0;
+    int S = 0;
+    for (int w : {want_w, 6, 4}) {
+        const ClusterVariant* best = nullptr;
+        for (int i = 0; i < count; ++i)
+            if (tab[i].nt == nt && tab[i].w == w && tab[i].vpt >= need && (!best || tab[i].vpt < best->vpt))
+                best = &tab[i];
+        if (!best) continue;
+        const uint32_t bytes = (uint32_t)chunk * 4u * eb;
+        const uint32_t padded = (uint32_t)nt * (uint32_t)best->vpt * 4u * eb;
+        stride = ((bytes > padded ? bytes : padded) + 127u) & ~127u;
+        S = 0;
+        while (S < kMaxStages && (size_t)(S + 1) * stride + cluster_ctrl_bytes(S + 1, nt) <= (size_t)smem_max) ++S;
+        if (S >= 2 * w) {
+            var = best;
+            break;
+        }
+    }
+    if (!var) return RK_EINVAL;
+    const size_t smem = (size_t)S * stride + cluster_ctrl_bytes(S, nt);
+    CParams cp;
+    cp.k = base;
+    cp.k.stages = S;
+    cp.k.stage_stride = stride;
+    cp.k.row_bytes = 0;   // per-CTA copy sizes are computed in the kernel
+    cp.chunk = chunk;
+    if (cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return RK_ECUDA;
+    if (C > 8 && cudaFuncSetAttribute(var->fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return RK_ECUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(a.q * C));
+    cfg.blockDim = dim3((unsigned)(nt + 32));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // the grid barrier needs every CTA resident at once: refuse what does not fit
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, (const void*)var->fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return RK_ECUDA;
+    }
+    if (clusters < a.q) return RK_ENOTCORESIDENT;
+    if (cudaLaunchKernelEx(&cfg, var->fn, cp) != cudaSuccess) return RK_ECUDA;
+    count_launch();
+    return RK_OK;
 }
 
 int launch_solve(const SolveArgs& a, cudaStream_t st) {
@@ -122,6 +193,7 @@ int launch_solve(const SolveArgs& a, cudaStream_t st) {
     p.row_bytes = row_bytes;
     p.stage_stride = stride;
 
+    if (a.opts.cluster_size > 1) return launch_cluster_solve(a, p, a.opts.cluster_size, st, smem_max);
     if (cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return RK_ECUDA;
