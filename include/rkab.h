@@ -254,6 +254,45 @@ int rkab_refine(const rk_plan *lowp, const float *A32, int64_t lda32, const floa
                 size_t ws_bytes, void *stream, int64_t *outer_done, double *last_metric);
 
 /* ------------------------------------------------------------------------ */
+/* Differentiation form: the adjoint of x = argmin ||A x - b|| (Eq.          */
+/* (ls_system)) for a loss L(x).  From the normal equations,                 */
+/*   grad_b = y,  grad_A = r g^T - y x^T,  r = b - A x,                      */
+/* where y is the minimum-norm solution of A^T y = dL/dx -- the limit of     */
+/* Kaczmarz started at y = 0 on the underdetermined system (Section 2.1) --  */
+/* and g solves the consistent system A g = y (so g = (A^T A)^{-1} dL/dx).   */
+/* ------------------------------------------------------------------------ */
+
+/* At (device, n x ldt, ldt >= m, ldt * 4 a multiple of 16) <- A^T for A (device float32,
+ * m x n, lda).  Asynchronous on `stream`. */
+int rk_transpose(const float *A, int64_t m, int64_t n, int64_t lda, float *At, int64_t ldt,
+                 void *stream);
+
+/* G (device, m x n, ldg) <- r g^T - y x^T for device vectors r, y (m) and g, x (n): the
+ * rank-2 gradient of A, written once.  Asynchronous on `stream`. */
+int rk_rank2(const float *r, const float *g, const float *y, const float *x, int64_t m, int64_t n,
+             float *G, int64_t ldg, void *stream);
+
+/* Bytes of device workspace rkab_adjoint needs. */
+size_t rk_adjoint_workspace_bytes(const rk_plan *plan_A, const rk_plan *plan_At, int q);
+
+/* Backward pass of the least-squares solve at the point x (device, n floats):
+ *   plan_A   float32 plan of A (m x n); plan_At float32 plan of A^T (n x m, e.g. from
+ *            rk_transpose); both must outlive the call
+ *   b        device, m floats;  gx device, n floats: dL/dx at x
+ *   y-solve  RKAB on A^T y = gx from y = 0: q workers, alpha_t, rounds_t, opts_t (Philox
+ *            stream id 1; cluster_size and lookahead are honoured)
+ *   g-solve  RKAB on A g = y from g = 0: q, alpha, rounds, opts (stream id 2)
+ *   grad_b   device, m floats <- y;  g device, n floats <- g
+ *   grad_A   device, m x n (ldg) <- r g^T - y x^T with r = b - A x (float64-accumulated)
+ * Synchronises `stream` at the end and returns RK_OK or the first error (device status of
+ * either solve included). */
+int rkab_adjoint(const rk_plan *plan_A, const rk_plan *plan_At, const float *b, const float *x,
+                 const float *gx, int q, int64_t alpha_t, int64_t rounds_t, int64_t alpha,
+                 int64_t rounds, uint64_t seed, const rk_opts *opts_t, const rk_opts *opts,
+                 float *grad_b, float *g, float *grad_A, int64_t ldg, void *workspace,
+                 size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Residual of Eq. (system) / Eq. (ls_system) with float32 A and float64     */
 /* accumulation:  r = b - A x,  ||r||_2  and  ||A^T r||_2.                   */
 /* ------------------------------------------------------------------------ */

@@ -334,6 +334,26 @@ def lstsq_qr(A, b):
     return np.linalg.solve(R, Q.T @ np.asarray(b, np.float64))
 
 
+def lstsq_adjoint(A, b, x, x_t):
+    """FP64 adjoint of x_LS(A, b) for L = 0.5 ||x - x_t||^2, evaluated at the point x:
+    g = (A^T A)^{-1} (x - x_t) through the QR factor (R^T R = A^T A), y = A g,
+    r = b - A x; returns (grad_A = r g^T - y x^T, grad_b = y, g)."""
+    A64 = np.asarray(A, np.float64)
+    x = np.asarray(x, np.float64)
+    gx = x - np.asarray(x_t, np.float64)
+    _, R = np.linalg.qr(A64, mode="reduced")
+    g = np.linalg.solve(R, np.linalg.solve(R.T, gx))
+    y = A64 @ g
+    r = np.asarray(b, np.float64) - A64 @ x
+    return np.outer(r, g) - np.outer(y, x), y, g
+
+
+def lstsq_loss(A, b, x_t):
+    """L(A, b) = 0.5 ||x_LS(A, b) - x_t||^2 in FP64 (QR)."""
+    x = lstsq_qr(A, b)
+    return 0.5 * float(np.sum((x - np.asarray(x_t, np.float64)) ** 2))
+
+
 def cgls(A, b, x0=None, tol=1e-14, maxiter=10000):
     """Conjugate gradients on the normal equations (CGLS), FP64; the solver the
     paper names for x_LS of its inconsistent data set (Section 3.1)."""

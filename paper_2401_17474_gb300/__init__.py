@@ -6,7 +6,10 @@ The CUDA library must be built first (``build.build()``); importing the
 binding's entry points raises if it is missing.  There is no CPU path.
 """
 from .api import (  # noqa: F401
+    Adjoint,
+    AdjointConfig,
     Plan,
+    RKABLstsq,
     Refiner,
     Residual,
     RkError,
@@ -15,10 +18,13 @@ from .api import (  # noqa: F401
     launch_count,
     make_opts,
     quantize,
+    rank2,
     rk_residual,
     rk_sample_indices,
     rk_setup,
     rka_solve,
     rkab_refine,
+    rkab_lstsq,
     rkab_solve,
+    transpose,
 )

@@ -76,6 +76,15 @@ _SIG = {
                                    ctypes.POINTER(RkOpts), _V, ctypes.c_size_t, _V,
                                    ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_double)]),
+    "rk_transpose": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _V,
+                                    ctypes.c_int64, _V]),
+    "rk_rank2": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_int64, ctypes.c_int64, _V, ctypes.c_int64,
+                                _V]),
+    "rk_adjoint_workspace_bytes": (ctypes.c_size_t, [_V, _V, ctypes.c_int]),
+    "rkab_adjoint": (ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+                                    ctypes.POINTER(RkOpts), ctypes.POINTER(RkOpts), _V, _V, _V,
+                                    ctypes.c_int64, _V, ctypes.c_size_t, _V]),
     "rk_residual_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     "rk_residual": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _V, _V,
                                    _V, _V, ctypes.c_int, _V, ctypes.c_size_t, _V]),

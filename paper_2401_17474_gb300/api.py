@@ -308,3 +308,120 @@ def rk_residual(A: torch.Tensor, b, x, want_atr=True, stream=None):
 def launch_count() -> int:
     """Kernel launches this process has enqueued through the library."""
     return int(_lib.load().rk_launch_count())
+
+
+# --------------------------------------------------------------------------
+# Differentiation form
+# --------------------------------------------------------------------------
+def transpose(A: torch.Tensor, stream=None) -> torch.Tensor:
+    """A^T of a float32 CUDA matrix, rows padded to 16 bytes (returns an (n, m) view)."""
+    if A.dtype != torch.float32 or A.stride(1) != 1 or not A.is_cuda:
+        raise ValueError("A must be a float32 CUDA matrix with unit column stride")
+    m, n = A.shape
+    ldt = (m + 3) // 4 * 4
+    At = torch.empty((n, ldt), dtype=torch.float32, device=A.device)
+    if ldt > m:
+        At[:, m:].zero_()
+    check(_lib.load().rk_transpose(_ptr(A), m, n, A.stride(0), _ptr(At), ldt, _stream(stream)),
+          "rk_transpose")
+    return At[:, :m]
+
+
+def rank2(r, g, y, x, out=None, stream=None) -> torch.Tensor:
+    """G = r g^T - y x^T (float32, m x n)."""
+    m, n = r.numel(), g.numel()
+    ldg = (n + 3) // 4 * 4
+    G = out if out is not None else torch.empty((m, ldg), dtype=torch.float32, device=r.device)[:, :n]
+    check(_lib.load().rk_rank2(_ptr(r), _ptr(g), _ptr(y), _ptr(x), m, n, _ptr(G), G.stride(0),
+                               _stream(stream)), "rk_rank2")
+    return G
+
+
+@dataclass
+class AdjointConfig:
+    """Parameters of the two solves of the backward pass."""
+    q: int = 8
+    alpha_t: int = 0          # projections per worker per round on A^T (0: its row count n)
+    rounds_t: int = 40
+    alpha: int = 0            # projections per worker per round on A g = y (0: n)
+    rounds: int = 40
+    seed: int = 1
+    cluster_size_t: int = 0   # CTAs per worker on A^T (long rows of length m)
+    cluster_size: int = 0
+    lookahead: int = 0
+
+
+class Adjoint:
+    """Plans of A and A^T and the workspace of rkab_adjoint."""
+
+    def __init__(self, plan_A: Plan, cfg: AdjointConfig, stream=None):
+        self.plan_A = plan_A
+        self.cfg = cfg
+        self.At = transpose(plan_A.A, stream)
+        self.plan_At = Plan(self.At, "f32", None, stream)
+        nbytes = _lib.load().rk_adjoint_workspace_bytes(plan_A.handle, self.plan_At.handle, cfg.q)
+        if nbytes == 0:
+            raise RkError(_lib.RK_EINVAL, "rk_adjoint_workspace_bytes")
+        self.ws = _workspace(nbytes, plan_A.device)
+
+    def backward(self, b, x, gx, stream=None):
+        """(grad_A, grad_b, g) at the point x for dL/dx = gx."""
+        m, n = self.plan_A.m, self.plan_A.n
+        c = self.cfg
+        dev = self.plan_A.device
+        grad_b = torch.empty(m, dtype=torch.float32, device=dev)
+        g = torch.empty(n, dtype=torch.float32, device=dev)
+        ldg = (n + 3) // 4 * 4
+        grad_A = torch.empty((m, ldg), dtype=torch.float32, device=dev)[:, :n]
+        ot = make_opts(check_every=0, cluster_size=c.cluster_size_t, lookahead=c.lookahead)
+        oa = make_opts(check_every=0, cluster_size=c.cluster_size, lookahead=c.lookahead)
+        check(_lib.load().rkab_adjoint(self.plan_A.handle, self.plan_At.handle, _ptr(b), _ptr(x),
+                                       _ptr(gx), c.q, c.alpha_t or n, c.rounds_t, c.alpha or n,
+                                       c.rounds, c.seed, ctypes.byref(ot), ctypes.byref(oa),
+                                       _ptr(grad_b), _ptr(g), _ptr(grad_A), grad_A.stride(0),
+                                       _ptr(self.ws), self.ws.numel(), _stream(stream)),
+              "rkab_adjoint")
+        return grad_A, grad_b, g
+
+
+class RKABLstsq(torch.autograd.Function):
+    """x = RKAB least-squares solve of A x ~ b (forward); backward by the adjoint:
+    grad_b = y (minimum-norm Kaczmarz solution of A^T y = dL/dx from y = 0),
+    grad_A = r g^T - y x^T with A g = y and r = b - A x."""
+
+    @staticmethod
+    def forward(ctx, A, b, q, alpha, schedule, seed, cluster_size, adj_cfg):
+        plan = Plan(A.detach())
+        bb = b.detach().contiguous()
+        x = torch.zeros(plan.n, dtype=torch.float32, device=plan.device)
+        round0 = 0
+        # phases of decreasing relaxation continue one stream of draws; with
+        # draws proportional to ||A_i||^2 the expected update is
+        # omega/||A||_F^2 A^T (b - A x), zero at x_LS, and the spread around it
+        # (the convergence horizon) shrinks with omega
+        for omega, rounds in schedule:
+            x, _ = rkab_solve(plan, bb, x, q=q, alpha=alpha, rounds=rounds, seed=seed,
+                              omega=omega, round0=round0, check_every=0,
+                              cluster_size=cluster_size)
+            round0 += rounds
+        ctx.plan = plan
+        ctx.adj_cfg = adj_cfg
+        ctx.save_for_backward(b, x)
+        return x
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        b, x = ctx.saved_tensors
+        adj = Adjoint(ctx.plan, ctx.adj_cfg)
+        grad_A, grad_b, _ = adj.backward(b.detach().contiguous(), x.detach(),
+                                         grad_x.detach().contiguous().to(torch.float32))
+        return grad_A, grad_b, None, None, None, None, None, None
+
+
+def rkab_lstsq(A, b, q=8, alpha=0, rounds=40, seed=0, cluster_size=0, adjoint=None,
+               schedule=None):
+    """Differentiable RKAB least-squares solve (see RKABLstsq).  `schedule` is a list of
+    (omega, rounds) phases (default: [(1.0, rounds)])."""
+    cfg = adjoint if adjoint is not None else AdjointConfig()
+    sched = tuple(schedule) if schedule is not None else ((1.0, rounds),)
+    return RKABLstsq.apply(A, b, q, alpha or A.shape[1], sched, seed, cluster_size, cfg)

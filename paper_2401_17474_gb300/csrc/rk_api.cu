@@ -278,6 +278,61 @@ int rkab_refine(const rk_plan* lowp, const float* A32, int64_t lda32, const floa
                       workspace, static_cast<cudaStream_t>(stream), outer_done, last_metric);
 }
 
+int rk_transpose(const float* A, int64_t m, int64_t n, int64_t lda, float* At, int64_t ldt,
+                 void* stream) {
+    if (!A || !At || m < 1 || n < 1 || lda < n || ldt < m) return RK_EINVAL;
+    if (!aligned16(At) || (ldt * 4) % 16 != 0) return RK_EALIGN;
+    return launch_transpose(A, m, n, lda, At, ldt, static_cast<cudaStream_t>(stream));
+}
+
+int rk_rank2(const float* r, const float* g, const float* y, const float* x, int64_t m, int64_t n,
+             float* G, int64_t ldg, void* stream) {
+    if (!r || !g || !y || !x || !G || m < 1 || n < 1 || ldg < n) return RK_EINVAL;
+    if (!aligned16(G) || (ldg * 4) % 16 != 0) return RK_EALIGN;
+    return launch_rank2(r, g, y, x, m, n, G, ldg, static_cast<cudaStream_t>(stream));
+}
+
+static bool valid_opts(const rk_opts& o) {
+    return o.omega > 0.0f && o.omega < 2.0f && o.check_every >= 0 && o.round0 >= 0 &&
+           o.timeout_s > 0.0 && !(o.criterion == 1 && !o.x_ref) && o.criterion >= 0 &&
+           o.criterion <= 1 &&
+           (o.lookahead == 0 || o.lookahead == 1 || o.lookahead == 2 || o.lookahead == 4 ||
+            o.lookahead == 6) &&
+           o.cluster_size >= 0 && o.cluster_size <= 16 && (o.cluster_size & (o.cluster_size - 1)) == 0;
+}
+
+size_t rk_adjoint_workspace_bytes(const rk_plan* plan_A, const rk_plan* plan_At, int q) {
+    if (!plan_A || !plan_At || q < 1) return 0;
+    return adjoint_ws_bytes(&plan_A->p, &plan_At->p, q);
+}
+
+int rkab_adjoint(const rk_plan* plan_A, const rk_plan* plan_At, const float* b, const float* x,
+                 const float* gx, int q, int64_t alpha_t, int64_t rounds_t, int64_t alpha,
+                 int64_t rounds, uint64_t seed, const rk_opts* opts_t, const rk_opts* opts,
+                 float* grad_b, float* g, float* grad_A, int64_t ldg, void* workspace,
+                 size_t ws_bytes, void* stream) {
+    if (!plan_A || !plan_At || !b || !x || !gx || !grad_b || !g || !grad_A || !workspace ||
+        q < 1 || alpha_t < 1 || rounds_t < 1 || alpha < 1 || rounds < 1)
+        return RK_EINVAL;
+    const Plan& pa = plan_A->p;
+    const Plan& pt = plan_At->p;
+    if (pa.dt != RK_F32 || pt.dt != RK_F32 || pt.m != pa.n || pt.n != pa.m || ldg < pa.n)
+        return RK_EINVAL;
+    if (!aligned16(grad_A) || (ldg * 4) % 16 != 0 || ((uintptr_t)workspace & 255u) != 0)
+        return RK_EALIGN;
+    rk_opts ot, oa;
+    rk_opts_default(&ot);
+    rk_opts_default(&oa);
+    if (opts_t) ot = *opts_t;
+    if (opts) oa = *opts;
+    ot.criterion = 0;
+    oa.criterion = 0;
+    if (!valid_opts(ot) || !valid_opts(oa)) return RK_EINVAL;
+    if (ws_bytes < adjoint_ws_bytes(&pa, &pt, q)) return RK_EWORKSPACE;
+    return run_adjoint(&pa, &pt, b, x, gx, q, alpha_t, rounds_t, alpha, rounds, seed, ot, oa,
+                       grad_b, grad_A, ldg, g, workspace, static_cast<cudaStream_t>(stream));
+}
+
 size_t rk_residual_workspace_bytes(int64_t m, int64_t n) {
     if (m < 1 || n < 1) return 0;
     return residual_ws_bytes(m, n);

@@ -104,6 +104,16 @@ int run_refine(const Plan* lowp, const float* A32, int64_t lda32, const float* b
                uint64_t seed, const rk_opts& o, void* ws, cudaStream_t st, int64_t* outer_done,
                double* last_metric);
 
+int launch_transpose(const float* A, int64_t m, int64_t n, int64_t lda, float* At, int64_t ldt,
+                     cudaStream_t st);
+int launch_rank2(const float* r, const float* g, const float* y, const float* x, int64_t m, int64_t n,
+                 float* G, int64_t ldg, cudaStream_t st);
+size_t adjoint_ws_bytes(const Plan* pa, const Plan* pt, int q);
+int run_adjoint(const Plan* pa, const Plan* pt, const float* b, const float* x, const float* gx,
+                int q, int64_t alpha_t, int64_t rounds_t, int64_t alpha, int64_t rounds, uint64_t seed,
+                const rk_opts& ot, const rk_opts& oa, float* grad_b, float* grad_A, int64_t ldg,
+                float* g_out, void* ws, cudaStream_t st);
+
 void count_launch(int k = 1);
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
