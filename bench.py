@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU work of the oracle baseline sample")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the per-cell, precision and adjoint measurements")
     return ap.parse_args()
 
 
@@ -77,8 +79,10 @@ def load_peaks():
 
 
 def kernel_hash():
+    """Hash of the device source of the one-CTA solve kernel (rk_solve_kernel.cuh,
+    rk_common.cuh): a recorded DRAM traffic is used only for the kernel it was taken on."""
     h = hashlib.sha1()
-    for f in ("rk_solve.cu", "rk_common.cuh"):
+    for f in ("rk_solve_kernel.cuh", "rk_common.cuh"):
         with open(os.path.join(ROOT, "paper_2401_17474_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -241,6 +245,108 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# Extra measurements on the same GPU (time to tolerance of other cells, the
+# precision form, the differentiation form); each is timed with CUDA events on
+# the launching stream after a warm-up run.
+# ---------------------------------------------------------------------------
+def _timed(fn, reps=2):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return best
+
+
+def extra_cells(rk, plan, b, xs, n, tol, max_rounds):
+    """Time to tolerance of the configurations of the benchmark's cell list and of RK."""
+    import torch
+    x0 = torch.zeros(n, dtype=torch.float32, device=b.device)
+    x = torch.empty_like(x0)
+    out = {}
+    cells = [("q132_alpha_n", 132, n, 0), ("q132_alpha_n/10", 132, n // 10, 0),
+             ("q32_alpha_n", 32, n, 0), ("q8_alpha_n", 8, n, 0),
+             ("q8_alpha_n_cluster16", 8, n, 16), ("q32_alpha_n_cluster4", 32, n, 4),
+             ("rk_q1", 1, n, 0), ("rk_q1_cluster16", 1, n, 16)]
+    for name, q, alpha, C in cells:
+        try:
+            s = rk.Solver(plan, q)
+            o = rk.make_opts(check_every=1, tol=tol, x_ref=xs, cluster_size=C)
+            t = _timed(lambda: s.launch(b, x0, x, alpha, max_rounds * (n // alpha), 0, o))
+            inf = s.info()
+            out[name] = {"ms": round(t, 2), "rounds": inf.rounds_done, "metric": inf.last_metric,
+                         "row_proj": q * alpha * inf.rounds_done, "status": inf.status}
+        except Exception as e:  # a cell that cannot run on this device is reported, not fatal
+            out[name] = {"error": str(e)}
+    return out
+
+
+def extra_precision(rk, A, plan32, b, xs, n, q, alpha, tol):
+    """Time to tolerance: plain FP32 RKAB vs BF16 / FP8 stored rows + refinement."""
+    import torch
+    x0 = torch.zeros(n, dtype=torch.float32, device=b.device)
+    x = torch.empty_like(x0)
+    out = {}
+    s = rk.Solver(plan32, q)
+    o = rk.make_opts(check_every=1, tol=tol, x_ref=xs)
+    t = _timed(lambda: s.launch(b, x0, x, alpha, 400, 0, o))
+    out["fp32_plain"] = {"ms": round(t, 2), "rounds": s.info().rounds_done,
+                         "metric": s.info().last_metric}
+    for kind in ("f32", "bf16", "fp8"):
+        try:
+            if kind == "f32":
+                lowp = plan32
+            else:
+                Aq, sc = rk.quantize(A, kind)
+                lowp = rk.rk_setup(Aq, kind, sc)
+            ref = rk.Refiner(lowp, q)
+            oo = rk.make_opts(check_every=0, tol=tol, x_ref=xs)
+            holder = {}
+
+            def go():
+                holder["i"] = ref.run(A, b, x0, x, alpha, 4, 40, 0, oo)
+            t = _timed(go)
+            out[f"{kind}_refine"] = {"ms": round(t, 2), "outer": holder["i"].outer_done,
+                                     "inner_rounds": 4, "metric": holder["i"].last_metric,
+                                     "bytes_per_row": n * {"f32": 4, "bf16": 2, "fp8": 1}[kind]}
+        except Exception as e:
+            out[f"{kind}_refine"] = {"error": str(e)}
+    return out
+
+
+def extra_adjoint(rk, dev, seed):
+    """Backward pass of the differentiation workload 50000 x 5000 (b = A x* + N(0, 1e-3^2),
+    L = 0.5 ||x - x_t||^2): A^T copy and plan, minimum-norm solve on A^T (16-CTA clusters),
+    solve of A g = y, residual, rank-2 gradient of A."""
+    import torch
+
+    import rk_inputs
+    m, n = 50000, 5000
+    A, b, xs = rk_inputs.gaussian_system_torch(m, n, seed=seed + 7, noise=1e-3, device=str(dev))
+    xt = torch.randn(n, generator=torch.Generator(device=dev).manual_seed(5), device=dev)
+    plan = rk.rk_setup(A)
+    x, _ = rk.rkab_solve(plan, b, q=16, alpha=n, rounds=30, seed=seed, check_every=0)
+    cfg = rk.AdjointConfig(q=8, alpha_t=n, rounds_t=30, alpha=n, rounds=30, seed=seed + 1,
+                           cluster_size_t=16)
+    t0 = time.perf_counter()
+    adj = rk.Adjoint(plan, cfg)
+    torch.cuda.synchronize()
+    t_setup = (time.perf_counter() - t0) * 1e3
+    gx = x - xt
+    t = _timed(lambda: adj.backward(b, x, gx), reps=2)
+    return {"workload": f"lstsq_adjoint_{m}x{n}", "backward_ms": round(t, 2),
+            "transpose_and_plan_ms": round(t_setup, 2), "q": 8, "rounds_t": 30, "rounds_g": 30,
+            "grad_A_bytes": m * n * 4}
+
+
+# ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -340,7 +446,7 @@ def run_ours(args):
     traffic = None if traffic_pp is None else traffic_pp * q * alpha * rounds_t
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "rkab_kernel<512,5>", "kernel_ms": 1e3 * kmean_s,
+                "kernel": "rkab_kernel (one CTA per worker)", "kernel_ms": 1e3 * kmean_s,
                 "algorithmic_bytes": alg}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -377,6 +483,17 @@ def run_ours(args):
                "d2h_bytes_per_step": n * 4, "ms_per_step": e_ms / e2e_steps}
         del A_h, A_d
 
+    extras = {}
+    if not args.no_extras and rank == 0:
+        for key, fn in (("cells", lambda: extra_cells(rk, plan0, b, xs, n, args.tol, 40)),
+                        ("precision", lambda: extra_precision(rk, A, plan0, b, xs, n, q, alpha,
+                                                              args.tol)),
+                        ("adjoint", lambda: extra_adjoint(rk, dev, args.seed))):
+            try:
+                extras[key] = fn()
+            except Exception as e:
+                extras[key] = {"error": str(e)}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         A_np = A.cpu().numpy()
@@ -399,6 +516,10 @@ def run_ours(args):
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu,
         }
+        if extras:
+            line["config"]["time_to_tol_cells"] = extras.get("cells")
+            line["precision"] = extras.get("precision")
+            line["adjoint"] = extras.get("adjoint")
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -9,6 +9,8 @@
 
 namespace rk {
 
+static size_t elem_size(rk_dtype dt) { return dt == RK_F32 ? 4 : (dt == RK_BF16 ? 2 : 1); }
+
 __global__ void sample_indices_kernel(const uint64_t* __restrict__ thr64,
                                       const uint32_t* __restrict__ alias, uint64_t m,
                                       uint64_t seed, uint32_t worker, uint32_t stream_id,
@@ -43,8 +45,6 @@ static const SolveVariant* pick_variant(rk_dtype dt, int n4, int w) {
 }
 
 static const int kMaxStages = 16;
-
-static size_t elem_size(rk_dtype dt) { return dt == RK_F32 ? 4 : (dt == RK_BF16 ? 2 : 1); }
 
 static int stages_for(uint32_t stride, int nt, int smem_max) {
     int S = 0;
@@ -124,6 +124,42 @@ static int launch_cluster_solve(const SolveArgs& a, const KParams& base, int C, 
     return RK_OK;
 }
 
+static KParams base_params(const SolveArgs& a) {
+    const Plan* pl = a.plan;
+    KParams p{};
+    p.A = static_cast<const uint8_t*>(pl->A);
+    p.lda_bytes = pl->lda * (int64_t)elem_size(pl->dt);
+    p.m = (uint64_t)pl->m;
+    p.n = (int)pl->n;
+    p.n4 = (int)((pl->n + 3) / 4);
+    p.b = a.b;
+    p.inv = pl->ws.inv;
+    p.row_scale = pl->row_scale;
+    p.thr64 = pl->ws.thr64;
+    p.alias = pl->ws.alias;
+    p.x0 = a.x0;
+    p.x = a.x;
+    p.V = a.V;
+    p.ldv = a.ldv;
+    p.xbuf = a.V + (size_t)a.q * (size_t)a.ldv;
+    p.q = a.q;
+    p.alpha = a.alpha;
+    p.rounds = a.rounds;
+    p.round0 = a.opts.round0;
+    p.seed = a.seed;
+    p.stream_id = a.opts.stream_id;
+    p.same_stream = a.opts.same_stream;
+    p.omega = a.opts.omega;
+    p.x_ref = a.opts.x_ref;
+    p.tol = a.opts.tol;
+    p.check_every = a.opts.check_every;
+    p.criterion = a.opts.criterion;
+    p.info = a.info;
+    p.setup = pl->ws.info;
+    p.timeout_ns = (uint64_t)(a.opts.timeout_s * 1e9);
+    return p;
+}
+
 int launch_solve(const SolveArgs& a, cudaStream_t st) {
     const Plan* pl = a.plan;
     const int n4 = (int)((pl->n + 3) / 4);
@@ -131,6 +167,7 @@ int launch_solve(const SolveArgs& a, cudaStream_t st) {
     cudaGetDevice(&dev);
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (a.opts.cluster_size > 1) return launch_cluster_solve(a, base_params(a), a.opts.cluster_size, st, smem_max);
     // slices of 4 elements; the copy is rounded up to 16 bytes, which stays inside
     // the row's lda extent because lda * element size is a multiple of 16
     const uint32_t row_bytes = ((uint32_t)n4 * 4u * (uint32_t)elem_size(pl->dt) + 15u) & ~15u;
@@ -158,42 +195,11 @@ int launch_solve(const SolveArgs& a, cudaStream_t st) {
     if (!var || S < 2) return RK_EINVAL;
     const size_t smem = (size_t)S * stride + solve_ctrl_bytes(S, var->nt);
 
-    KParams p{};
-    p.A = static_cast<const uint8_t*>(pl->A);
-    p.lda_bytes = pl->lda * (int64_t)elem_size(pl->dt);
-    p.m = (uint64_t)pl->m;
-    p.n = (int)pl->n;
-    p.n4 = n4;
-    p.b = a.b;
-    p.inv = pl->ws.inv;
-    p.row_scale = pl->row_scale;
-    p.thr64 = pl->ws.thr64;
-    p.alias = pl->ws.alias;
-    p.x0 = a.x0;
-    p.x = a.x;
-    p.V = a.V;
-    p.ldv = a.ldv;
-    p.xbuf = a.V + (size_t)a.q * (size_t)a.ldv;
-    p.q = a.q;
-    p.alpha = a.alpha;
-    p.rounds = a.rounds;
-    p.round0 = a.opts.round0;
-    p.seed = a.seed;
-    p.stream_id = a.opts.stream_id;
-    p.same_stream = a.opts.same_stream;
-    p.omega = a.opts.omega;
-    p.x_ref = a.opts.x_ref;
-    p.tol = a.opts.tol;
-    p.check_every = a.opts.check_every;
-    p.criterion = a.opts.criterion;
-    p.info = a.info;
-    p.setup = pl->ws.info;
-    p.timeout_ns = (uint64_t)(a.opts.timeout_s * 1e9);
+    KParams p = base_params(a);
     p.stages = S;
     p.row_bytes = row_bytes;
     p.stage_stride = stride;
 
-    if (a.opts.cluster_size > 1) return launch_cluster_solve(a, p, a.opts.cluster_size, st, smem_max);
     if (cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return RK_ECUDA;
