@@ -268,40 +268,43 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
                     const uint32_t pr = sr >= S ? (ph ^ 1u) : ph;
                     if (rr < wc) got = wait_parity(&full[sg[rr]], pr, p.timeout_ns, status) && got;
                 }
-                float acc[kNVP];
+                // packed accumulators: element pairs (x,y) and (z,w) of the slices are
+                // accumulated separately and folded before the reduction
+                float2 acc2[NV];
 #pragma unroll
-                for (int u = 0; u < kNVP; ++u) acc[u] = 0.f;
+                for (int u = 0; u < NV; ++u) acc2[u] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int k = 0; k < VPT; ++k) {
-                    float4 aq[W];
+                    float2 alo[W], ahi[W];
 #pragma unroll
                     for (int rr = 0; rr < W; ++rr) {
-                        aq[rr] = rr < wc ? slice<ELT>(stages + (size_t)sg[rr] * p.stage_stride, tid + k * NT, k, tail_k, rem)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 aq = rr < wc ? slice<ELT>(stages + (size_t)sg[rr] * p.stage_stride, tid + k * NT, k, tail_k, rem)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                        alo[rr] = make_float2(aq.x, aq.y);
+                        ahi[rr] = make_float2(aq.z, aq.w);
                     }
+                    const float2 vlo = make_float2(v[k].x, v[k].y), vhi = make_float2(v[k].z, v[k].w);
+                    const float2 dlo = make_float2(d[k].x, d[k].y), dhi = make_float2(d[k].z, d[k].w);
 #pragma unroll
                     for (int rr = 0; rr < W; ++rr) {
-                        float g = acc[rr];
-                        g = fmaf(aq[rr].x, v[k].x, g);
-                        g = fmaf(aq[rr].y, v[k].y, g);
-                        g = fmaf(aq[rr].z, v[k].z, g);
-                        g = fmaf(aq[rr].w, v[k].w, g);
-                        g = fmaf(aq[rr].x, d[k].x, g);
-                        g = fmaf(aq[rr].y, d[k].y, g);
-                        g = fmaf(aq[rr].z, d[k].z, g);
-                        g = fmaf(aq[rr].w, d[k].w, g);
-                        acc[rr] = g;
+                        float2 g = acc2[rr];
+                        g = __ffma2_rn(alo[rr], vlo, g);
+                        g = __ffma2_rn(ahi[rr], vhi, g);
+                        g = __ffma2_rn(alo[rr], dlo, g);
+                        g = __ffma2_rn(ahi[rr], dhi, g);
+                        acc2[rr] = g;
 #pragma unroll
                         for (int ll = 0; ll < rr; ++ll) {
-                            float h = acc[CGroup<W>::gram(rr, ll)];
-                            h = fmaf(aq[rr].x, aq[ll].x, h);
-                            h = fmaf(aq[rr].y, aq[ll].y, h);
-                            h = fmaf(aq[rr].z, aq[ll].z, h);
-                            h = fmaf(aq[rr].w, aq[ll].w, h);
-                            acc[CGroup<W>::gram(rr, ll)] = h;
+                            float2 h = acc2[CGroup<W>::gram(rr, ll)];
+                            h = __ffma2_rn(alo[rr], alo[ll], h);
+                            h = __ffma2_rn(ahi[rr], ahi[ll], h);
+                            acc2[CGroup<W>::gram(rr, ll)] = h;
                         }
                     }
                 }
+                float acc[kNVP];
+#pragma unroll
+                for (int u = 0; u < kNVP; ++u) acc[u] = u < NV ? acc2[u].x + acc2[u].y : 0.f;
                 // warp totals: lane u holds partial sum u of this warp
                 const float mine = reduce_scatter32(acc, lane);
                 wred[warp * kNVP + lane] = mine;
@@ -339,16 +342,17 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
                 }
 #pragma unroll
                 for (int k = 0; k < VPT; ++k) {
+                    float2 dlo = make_float2(d[k].x, d[k].y), dhi = make_float2(d[k].z, d[k].w);
 #pragma unroll
                     for (int rr = 0; rr < W; ++rr) {
                         if (rr < wc) {
                             const float4 aq = slice<ELT>(stages + (size_t)sg[rr] * p.stage_stride, tid + k * NT, k, tail_k, rem);
-                            d[k].x = fmaf(c[rr], aq.x, d[k].x);
-                            d[k].y = fmaf(c[rr], aq.y, d[k].y);
-                            d[k].z = fmaf(c[rr], aq.z, d[k].z);
-                            d[k].w = fmaf(c[rr], aq.w, d[k].w);
+                            const float2 cc = make_float2(c[rr], c[rr]);
+                            dlo = __ffma2_rn(cc, make_float2(aq.x, aq.y), dlo);
+                            dhi = __ffma2_rn(cc, make_float2(aq.z, aq.w), dhi);
                         }
                     }
+                    d[k] = make_float4(dlo.x, dlo.y, dhi.x, dhi.y);
                 }
                 __syncwarp();
                 if (lane == 0) {

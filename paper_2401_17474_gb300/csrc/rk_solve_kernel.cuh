@@ -540,23 +540,24 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
             const bool got = wait_parity(&full[s], ph, p.timeout_ns, status);
             const uint8_t* stg = stages + (size_t)s * p.stage_stride;
             const float4 mb = meta[s];   // b_i, 1/||A_i||^2, row scale
-            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-#define RK_FUSED_SLICE(LOADEXPR)                                          \
-            {                                                             \
-                const float4 ak = LOADEXPR;                               \
-                d[k].x = fmaf(cprev, a[k].x, d[k].x);                     \
-                d[k].y = fmaf(cprev, a[k].y, d[k].y);                     \
-                d[k].z = fmaf(cprev, a[k].z, d[k].z);                     \
-                d[k].w = fmaf(cprev, a[k].w, d[k].w);                     \
-                p0 = fmaf(ak.x, v[k].x, p0);                              \
-                p1 = fmaf(ak.y, v[k].y, p1);                              \
-                p2 = fmaf(ak.z, v[k].z, p2);                              \
-                p3 = fmaf(ak.w, v[k].w, p3);                              \
-                p0 = fmaf(ak.x, d[k].x, p0);                              \
-                p1 = fmaf(ak.y, d[k].y, p1);                              \
-                p2 = fmaf(ak.z, d[k].z, p2);                              \
-                p3 = fmaf(ak.w, d[k].w, p3);                              \
-                a[k] = ak;                                                \
+            // two packed accumulators (elements x,y and z,w of the slices); each
+            // packed FMA is two independent float32 FMAs
+            float2 p01 = make_float2(0.f, 0.f), p23 = make_float2(0.f, 0.f);
+            const float2 cc = make_float2(cprev, cprev);
+#define RK_FUSED_SLICE(LOADEXPR)                                                        \
+            {                                                                           \
+                const float4 ak = LOADEXPR;                                             \
+                const float2 dlo = __ffma2_rn(cc, make_float2(a[k].x, a[k].y),          \
+                                              make_float2(d[k].x, d[k].y));             \
+                const float2 dhi = __ffma2_rn(cc, make_float2(a[k].z, a[k].w),          \
+                                              make_float2(d[k].z, d[k].w));             \
+                const float2 alo = make_float2(ak.x, ak.y), ahi = make_float2(ak.z, ak.w); \
+                p01 = __ffma2_rn(alo, make_float2(v[k].x, v[k].y), p01);                \
+                p23 = __ffma2_rn(ahi, make_float2(v[k].z, v[k].w), p23);                \
+                p01 = __ffma2_rn(alo, dlo, p01);                                        \
+                p23 = __ffma2_rn(ahi, dhi, p23);                                        \
+                d[k] = make_float4(dlo.x, dlo.y, dhi.x, dhi.y);                         \
+                a[k] = ak;                                                              \
             }
             if (rem == 0) {
 #pragma unroll
@@ -568,7 +569,7 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
 #undef RK_FUSED_SLICE
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
-            float part = (p0 + p1) + (p2 + p3);
+            float part = (p01.x + p01.y) + (p23.x + p23.y);
 #pragma unroll
             for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
             if (lane == 0) red[rp * kRedSlots * 32 + warp] = part;
@@ -586,12 +587,14 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
             cprev = p.omega * (mb.x - mb.z * dot) * mb.y * mb.z;
             if (++s == p.stages) { s = 0; ph ^= 1u; }
         }
+        {
+            const float2 cc = make_float2(cprev, cprev);
 #pragma unroll
-        for (int k = 0; k < VPT; ++k) {
-            d[k].x = fmaf(cprev, a[k].x, d[k].x);
-            d[k].y = fmaf(cprev, a[k].y, d[k].y);
-            d[k].z = fmaf(cprev, a[k].z, d[k].z);
-            d[k].w = fmaf(cprev, a[k].w, d[k].w);
+            for (int k = 0; k < VPT; ++k) {
+                const float2 dlo = __ffma2_rn(cc, make_float2(a[k].x, a[k].y), make_float2(d[k].x, d[k].y));
+                const float2 dhi = __ffma2_rn(cc, make_float2(a[k].z, a[k].w), make_float2(d[k].z, d[k].w));
+                d[k] = make_float4(dlo.x, dlo.y, dhi.x, dhi.y);
+            }
         }
       } else {
         for (int64_t j = 0; j < p.alpha; ++j, ++t) {
