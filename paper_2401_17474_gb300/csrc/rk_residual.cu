@@ -1,5 +1,5 @@
 // rk_residual.cu -- residual of Eq. (system) / Eq. (ls_system) with float32 A
-// and float64 accumulation: r = b - A x, ||r||_2 and the normal-equation
+// and FP64-class accumulation: r = b - A x, ||r||_2 and the normal-equation
 // residual ||A^T r||_2.  All reductions run in a fixed order (warp butterfly,
 // then block partials summed in ascending block order), so results are the
 // same on every run.
@@ -39,7 +39,27 @@ static int atr_chunks(int64_t m, int64_t n) {
     return (int)(chunks < 1 ? 1 : chunks);
 }
 
-// One warp per row: r_i = b_i - sum_j a_ij x_j, products and sums in float64.
+// Exact product and compensated (TwoSum) accumulation in a pair of float32:
+// a x = p + e exactly (e = fma(a, x, -p)); (hi, lo) += p + e with the rounding
+// error of hi + p recovered by TwoSum (Knuth).  Over k terms the pair's error is
+// about 2^-46 sum|a_j x_j| (the float32 pair carries ~48 significant bits), which
+// is tighter than float64 recursive summation (k 2^-53 sum|a_j x_j|) once k > 2^7;
+// the pairs of the 32 lanes are then added in float64.
+// The _rn intrinsics are never contracted into fused multiply-adds, which the
+// error terms rely on.
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float a, float x) {
+    const float p = __fmul_rn(a, x);
+    const float e = fmaf(a, x, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// One warp per row: r_i = b_i - sum_j a_ij x_j with FP64-class accumulation
+// (compensated float32 pairs per lane, float64 across lanes) -- the float64 pipe
+// of the device is not needed per element, so the pass runs at memory speed.
 __global__ void __launch_bounds__(kResThreads) residual_rows_kernel(
     const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, const float* __restrict__ b,
     const float* __restrict__ x, double* __restrict__ r, double* __restrict__ rr_part) {
@@ -51,16 +71,17 @@ __global__ void __launch_bounds__(kResThreads) residual_rows_kernel(
          i += (int64_t)gridDim.x * (kResThreads / 32)) {
         const float* a = A + i * lda;
         const float4* a4 = reinterpret_cast<const float4*>(a);
-        double acc = 0.0;
+        float hi = 0.f, lo = 0.f;
         for (int64_t c = lane; c < n4; c += 32) {
-            const float4 v = __ldg(a4 + c);
+            const float4 v = __ldcs(a4 + c);   // streamed once: evict first
             const int64_t j = c * 4;
-            acc = fma((double)v.x, (double)__ldg(x + j), acc);
-            acc = fma((double)v.y, (double)__ldg(x + j + 1), acc);
-            acc = fma((double)v.z, (double)__ldg(x + j + 2), acc);
-            acc = fma((double)v.w, (double)__ldg(x + j + 3), acc);
+            df_acc(hi, lo, v.x, __ldg(x + j));
+            df_acc(hi, lo, v.y, __ldg(x + j + 1));
+            df_acc(hi, lo, v.z, __ldg(x + j + 2));
+            df_acc(hi, lo, v.w, __ldg(x + j + 3));
         }
-        for (int64_t j = n4 * 4 + lane; j < n; j += 32) acc = fma((double)__ldg(a + j), (double)__ldg(x + j), acc);
+        for (int64_t j = n4 * 4 + lane; j < n; j += 32) df_acc(hi, lo, __ldg(a + j), __ldg(x + j));
+        double acc = (double)hi + (double)lo;
 #pragma unroll
         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         const double ri = (double)__ldg(b + i) - acc;
