@@ -59,6 +59,12 @@ def parse():
                     help="target CPU work of the oracle baseline sample")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-cell, precision and adjoint measurements")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"],
+                    help="stored rows of the timed solve (bf16/fp8: quantised copy of A)")
+    ap.add_argument("--cluster", type=int, default=0,
+                    help="CTAs per worker of the timed solve (0/1: one CTA per worker)")
+    ap.add_argument("--lookahead", type=int, default=0,
+                    help="rows per look-ahead group of the timed solve (0: automatic)")
     return ap.parse_args()
 
 
@@ -374,11 +380,21 @@ def run_ours(args):
     setup_ws = torch.empty(rk.api._lib.load().rk_setup_workspace_bytes(m, n), dtype=torch.uint8,
                            device=dev)
     plan0 = rk.rk_setup(A, stream=stream, workspace=setup_ws)
+    if args.dtype == "f32":
+        A_solve, scale_solve = A, None
+    else:
+        A_solve, scale_solve = rk.quantize(A, args.dtype)
+    elem = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
     solver = rk.Solver(plan0, q)
-    opts = rk.make_opts(check_every=1, tol=args.tol, x_ref=xs)
+    opts = rk.make_opts(check_every=1, tol=args.tol, x_ref=xs, cluster_size=args.cluster,
+                        lookahead=args.lookahead)
 
     def step(record=None):
-        plan = rk.rk_setup(A, stream=stream, workspace=setup_ws)
+        if args.dtype == "f32":
+            plan = rk.rk_setup(A, stream=stream, workspace=setup_ws)
+        else:
+            plan = rk.rk_setup(A_solve, args.dtype, scale_solve, stream=stream,
+                               workspace=setup_ws)
         solver.plan = plan
         if record is not None:
             record[0].record(stream)
@@ -440,18 +456,20 @@ def run_ours(args):
     # roofline of the dominant kernel (the persistent solve), from its own events
     peak, peak_kind = load_peaks()
     kmean_s = sum(kern_ms) / len(kern_ms) / 1e3
-    alg = algorithmic_bytes(n, q, alpha, rounds_t)
+    alg = algorithmic_bytes(n, q, alpha, rounds_t, elem)
     achieved = alg / kmean_s / 1e9
-    traffic_pp = recorded_traffic("c2")
+    default_cfg = (m, n, q, alpha, args.dtype, args.cluster) == (80000, 10000, 132, 10000, "f32", 0)
+    traffic_pp = recorded_traffic("c2") if default_cfg else None
     traffic = None if traffic_pp is None else traffic_pp * q * alpha * rounds_t
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "rkab_kernel (one CTA per worker)", "kernel_ms": 1e3 * kmean_s,
-                "algorithmic_bytes": alg}
+                "kernel": ("rkab_cluster_kernel (%d CTAs per worker)" % args.cluster
+                           if args.cluster > 1 else "rkab_kernel (one CTA per worker)"),
+                "kernel_ms": 1e3 * kmean_s, "algorithmic_bytes": alg}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.dtype == "f32":
         A_h = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
         A_h.copy_(A)
         b_h = b.cpu().pin_memory()
@@ -472,7 +490,9 @@ def run_ours(args):
             pl = rk.rk_setup(A_d, stream=stream, workspace=setup_ws)
             solver.plan = pl
             solver.launch(b_d, x0, x, alpha, args.max_rounds, args.seed,
-                          rk.make_opts(check_every=1, tol=args.tol, x_ref=xs_d), stream)
+                          rk.make_opts(check_every=1, tol=args.tol, x_ref=xs_d,
+                                       cluster_size=args.cluster, lookahead=args.lookahead),
+                          stream)
             x_h.copy_(x, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize(dev)
@@ -501,13 +521,16 @@ def run_ours(args):
         cpu = cpu_baseline(A_np, b_np, q, args.seed, args.cpu_seconds)
 
     if rank == 0:
+        dname = "fp32" if args.dtype == "f32" else args.dtype
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"rkab_consistent_{m}x{n}_q{q}_alpha{alpha}_fp32",
+            "config": {"workload": f"rkab_consistent_{m}x{n}_q{q}_alpha{alpha}_{dname}"
+                                   + (f"_cluster{args.cluster}" if args.cluster > 1 else ""),
                        "m": m, "n": n, "q": q, "alpha": alpha, "tol": args.tol,
+                       "stored_rows": args.dtype, "cluster": args.cluster,
                        "criterion": "||x-x*||/||x*||, checked after every average",
                        "rounds_to_tol": rounds_t, "parallelism": f"replicas{ws}",
                        "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 4 / 1e9),
