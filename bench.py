@@ -65,6 +65,11 @@ def parse():
                     help="CTAs per worker of the timed solve (0/1: one CTA per worker)")
     ap.add_argument("--lookahead", type=int, default=0,
                     help="rows per look-ahead group of the timed solve (0: automatic)")
+    ap.add_argument("--workload", default="consistent", choices=["consistent", "lsq", "precision"],
+                    help="consistent: 80000 x 10000 to 1e-6 (default); lsq: 200000 x 20000 "
+                         "row-scaled inconsistent system, budget of rounds with the normal-equation "
+                         "criterion logged every round; precision: 1e6 x 16000, FP32 vs BF16/FP8 "
+                         "+ refinement to 1e-6")
     return ap.parse_args()
 
 
@@ -327,6 +332,45 @@ def extra_precision(rk, A, plan32, b, xs, n, q, alpha, tol):
     return out
 
 
+def extra_relaxed(rk, A, plan, b, xs, n, tol):
+    """Relaxed averaging (Section 2.3.1 and 3.4.2): RKA with the optimal uniform
+    weight alpha* of Eq. (best_alpha), from the spectrum estimated on the GPU
+    (rk_spectrum), and RKAB with a relaxation above 1 (the paper's alpha on every
+    inner projection; values taken from a sweep, the paper gives no a priori
+    value for RKAB)."""
+    import torch
+    x0 = torch.zeros(n, dtype=torch.float32, device=b.device)
+    x = torch.empty_like(x0)
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rk.spectrum(A, k=8)   # warm-up
+    e0.record()
+    sp = rk.spectrum(A, k=8)
+    e1.record()
+    torch.cuda.synchronize()
+    out["spectrum"] = {"ms": round(e0.elapsed_time(e1), 2), "lanczos_steps": sp.steps,
+                       "s_min": sp.s_min, "s_max": sp.s_max}
+    cells = [("rka_q132_alpha_star", 132, 1, rk.alpha_star(132, sp.s_min, sp.s_max), 20000),
+             ("rka_q152_alpha_star", 152, 1, rk.alpha_star(152, sp.s_min, sp.s_max), 20000),
+             ("rka_q32_alpha_star", 32, 1, rk.alpha_star(32, sp.s_min, sp.s_max), 40000),
+             ("rka_q132_omega1", 132, 1, 1.0, 400000),
+             ("rkab_q152_alpha20_omega24", 152, 20, 24.0, 4000),
+             ("rkab_q152_alpha50_omega16", 152, 50, 16.0, 2000),
+             ("rkab_q152_alpha10_omega32", 152, 10, 32.0, 6000)]
+    for name, q, alpha, omega, max_rounds in cells:
+        try:
+            s = rk.Solver(plan, q)
+            o = rk.make_opts(check_every=1, tol=tol, x_ref=xs, omega=omega)
+            t = _timed(lambda: s.launch(b, x0, x, alpha, max_rounds, 0, o), reps=1)
+            inf = s.info()
+            out[name] = {"ms": round(t, 2), "q": q, "alpha": alpha, "omega": round(omega, 4),
+                         "rounds": inf.rounds_done, "metric": inf.last_metric,
+                         "row_proj": q * alpha * inf.rounds_done, "status": inf.status}
+        except Exception as e:
+            out[name] = {"error": str(e)}
+    return out
+
+
 def extra_adjoint(rk, dev, seed):
     """Backward pass of the differentiation workload 50000 x 5000 (b = A x* + N(0, 1e-3^2),
     L = 0.5 ||x - x_t||^2): A^T copy and plan, minimum-norm solve on A^T (16-CTA clusters),
@@ -339,7 +383,7 @@ def extra_adjoint(rk, dev, seed):
     xt = torch.randn(n, generator=torch.Generator(device=dev).manual_seed(5), device=dev)
     plan = rk.rk_setup(A)
     x, _ = rk.rkab_solve(plan, b, q=16, alpha=n, rounds=30, seed=seed, check_every=0)
-    cfg = rk.AdjointConfig(q=8, alpha_t=n, rounds_t=30, alpha=n, rounds=30, seed=seed + 1,
+    cfg = rk.AdjointConfig(q=6, alpha_t=n, rounds_t=30, alpha=n, rounds=30, seed=seed + 1,
                            cluster_size_t=16)
     t0 = time.perf_counter()
     adj = rk.Adjoint(plan, cfg)
@@ -348,8 +392,159 @@ def extra_adjoint(rk, dev, seed):
     gx = x - xt
     t = _timed(lambda: adj.backward(b, x, gx), reps=2)
     return {"workload": f"lstsq_adjoint_{m}x{n}", "backward_ms": round(t, 2),
-            "transpose_and_plan_ms": round(t_setup, 2), "q": 8, "rounds_t": 30, "rounds_g": 30,
+            "transpose_and_plan_ms": round(t_setup, 2), "q": 6, "rounds_t": 30, "rounds_g": 30,
             "grad_A_bytes": m * n * 4}
+
+
+# ---------------------------------------------------------------------------
+# Other workloads of the benchmark list (each prints its own line)
+# ---------------------------------------------------------------------------
+def _base_line(args, metric, value, unit, ms_per_step, config, clk, launches, hib=True):
+    ws, _, _ = dist_env()
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": hib,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config, "clocks": clk, "gpu_launches": launches}
+
+
+def run_lsq(args, rk, dev):
+    """200000 x 20000, rows scaled by 10^U(-2,2), b = A x* + N(0, 1e-3^2): RKAB q = 132,
+    alpha = n; the criterion ||A^T r|| / (||A||_F ||r||) after every round (rk_residual,
+    float64-class accumulation), over a fixed budget of rounds (the criterion 1e-6 lies
+    beyond the horizon of RKAB on this system).  One step = one round + its criterion."""
+    import torch
+
+    import rk_inputs
+    m, n, q = 200000, 20000, args.q
+    alpha = args.alpha or n
+    A, b, _ = rk_inputs.gaussian_system_torch(m, n, seed=args.seed, noise=1e-3,
+                                              row_scale_decades=2.0, device=str(dev))
+    plan = rk.rk_setup(A)
+    T, L = plan.status()
+    fro = (T * 2.0 ** L) ** 0.5
+    solver = rk.Solver(plan, q)
+    res = rk.Residual(m, n, dev)
+    norms = torch.zeros(2, dtype=torch.float64, device=dev)
+    xa = torch.zeros(n, dtype=torch.float32, device=dev)
+    xb = torch.empty_like(xa)
+    opts0 = rk.make_opts(check_every=0)
+    rounds = args.steps + args.warmup
+    crit, kern = [], []
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0")
+    launches0 = rk.launch_count()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e_all0, e_all1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for r in range(rounds):
+        if r == args.warmup:
+            e_all0.record()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        o = rk.make_opts(check_every=0, round0=r)
+        e0.record()
+        solver.launch(b, xa, xb, alpha, 1, args.seed, o)
+        e1.record()
+        res.launch(A, b, xb, None, norms, True)
+        nr = norms.cpu().numpy()   # synchronises the stream
+        crit.append(float(nr[1] / (fro * nr[0])))
+        kern.append(e0.elapsed_time(e1))
+        if solver.info().status != 0:
+            raise rk.RkError(solver.info().status, "lsq round")
+        xa, xb = xb, xa
+    e_all1.record()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    total = e_all0.elapsed_time(e_all1)
+    units = q * alpha * args.steps
+    peak, kind = load_peaks()
+    kmean = sum(kern[args.warmup:]) / args.steps / 1e3
+    alg = algorithmic_bytes(n, q, alpha, 1)
+    line = _base_line(args, METRIC, units / (total / 1e3), UNIT, total / args.steps,
+                      {"workload": f"rkab_lsq_rowscaled_{m}x{n}_q{q}_alpha{alpha}_fp32",
+                       "m": m, "n": n, "q": q, "alpha": alpha, "noise": 1e-3,
+                       "row_scale": "10^U(-2,2)", "criterion": "||A^T r||/(||A||_F ||r||)",
+                       "criterion_per_round": crit, "rounds": rounds,
+                       "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 4 / 1e9)},
+                      clk, rk.launch_count() - launches0)
+    line["roofline"] = {"bound": "hbm", "achieved": alg / kmean / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": alg / kmean / 1e9 / peak, "traffic": None, "peak_kind": kind,
+                        "kernel": "rkab_kernel (one CTA per worker)", "kernel_ms": 1e3 * kmean}
+    return line
+
+
+def run_precision(args, rk, dev):
+    """1e6 x 16000 consistent system: plain FP32 RKAB (q = 132, alpha = n) against BF16 and
+    FP8 e4m3 stored rows with refinement on the FP32 master, time to ||x - x*||/||x*|| < 1e-6;
+    also RKA with the weight of Eq. (best_alpha) on each storage.  One step = the FP32
+    setup + solve to tolerance."""
+    import torch
+
+    import rk_inputs
+    m, n, q = 1000000, 16000, args.q
+    alpha = args.alpha or n
+    A, b, xs = rk_inputs.gaussian_system_torch(m, n, seed=args.seed, device=str(dev))
+    x0 = torch.zeros(n, dtype=torch.float32, device=dev)
+    x = torch.empty_like(x0)
+    plan = rk.rk_setup(A)
+    solver = rk.Solver(plan, q)
+    o = rk.make_opts(check_every=1, tol=args.tol, x_ref=xs)
+    for _ in range(args.warmup):
+        solver.launch(b, x0, x, alpha, args.max_rounds, args.seed, o)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0")
+    launches0 = rk.launch_count()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan = rk.rk_setup(A)
+        solver.plan = plan
+        solver.launch(b, x0, x, alpha, args.max_rounds, args.seed, o)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    launches = rk.launch_count() - launches0
+    total = e0.elapsed_time(e1)
+    inf = solver.info()
+    units = q * alpha * inf.rounds_done * args.steps
+    out = {"fp32_plain": {"ms": round(total / args.steps, 2), "rounds": inf.rounds_done,
+                          "metric": inf.last_metric}}
+    sp = rk.spectrum(A, k=8)
+    for kind in ("bf16", "fp8"):
+        try:
+            Aq, sc = rk.quantize(A, kind)
+            lowp = rk.rk_setup(Aq, kind, sc)
+            ref = rk.Refiner(lowp, q)
+            oo = rk.make_opts(check_every=0, tol=args.tol, x_ref=xs)
+            holder = {}
+
+            def go():
+                holder["i"] = ref.run(A, b, x0, x, alpha, 4, 40, args.seed, oo)
+            t = _timed(go, reps=1)
+            out[f"{kind}_refine"] = {"ms": round(t, 2), "outer": holder["i"].outer_done,
+                                     "inner_rounds": 4, "metric": holder["i"].last_metric}
+            del Aq, lowp, ref
+        except Exception as e:
+            out[f"{kind}_refine"] = {"error": str(e)}
+        torch.cuda.empty_cache()
+    s3 = rk.Solver(plan, 152)
+    o3 = rk.make_opts(check_every=1, tol=args.tol, x_ref=xs,
+                      omega=rk.alpha_star(152, sp.s_min, sp.s_max))
+    t = _timed(lambda: s3.launch(b, x0, x, 1, 40000, args.seed, o3), reps=1)
+    out["fp32_rka_q152_alpha_star"] = {"ms": round(t, 2), "rounds": s3.info().rounds_done,
+                                       "metric": s3.info().last_metric}
+    peak, kind = load_peaks()
+    line = _base_line(args, METRIC, units / (total / 1e3), UNIT, total / args.steps,
+                      {"workload": f"rkab_precision_{m}x{n}_q{q}_alpha{alpha}",
+                       "m": m, "n": n, "q": q, "alpha": alpha, "tol": args.tol,
+                       "time_to_tol": out,
+                       "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 4 / 1e9)},
+                      clk, launches)
+    alg = algorithmic_bytes(n, q, alpha, inf.rounds_done)
+    line["roofline"] = {"bound": "hbm", "achieved": alg / (total / args.steps / 1e3) / 1e9,
+                        "peak": peak, "unit": "GB/s",
+                        "frac": alg / (total / args.steps / 1e3) / 1e9 / peak, "traffic": None,
+                        "peak_kind": kind, "kernel": "rkab_kernel (setup + solve, one step)"}
+    return line
 
 
 # ---------------------------------------------------------------------------
@@ -370,6 +565,15 @@ def run_ours(args):
     import paper_2401_17474_gb300 as rk
     from paper_2401_17474_gb300 import build as rkbuild
     rkbuild.build()
+
+    if args.workload != "consistent":
+        if rank == 0:
+            fn = run_lsq if args.workload == "lsq" else run_precision
+            print(json.dumps(fn(args, rk, dev)), flush=True)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
 
     m, n, q = args.m, args.n, args.q
     alpha = args.alpha or n
@@ -508,6 +712,7 @@ def run_ours(args):
         for key, fn in (("cells", lambda: extra_cells(rk, plan0, b, xs, n, args.tol, 40)),
                         ("precision", lambda: extra_precision(rk, A, plan0, b, xs, n, q, alpha,
                                                               args.tol)),
+                        ("relaxed", lambda: extra_relaxed(rk, A, plan0, b, xs, n, args.tol)),
                         ("adjoint", lambda: extra_adjoint(rk, dev, args.seed))):
             try:
                 extras[key] = fn()
@@ -543,6 +748,7 @@ def run_ours(args):
             line["config"]["time_to_tol_cells"] = extras.get("cells")
             line["precision"] = extras.get("precision")
             line["adjoint"] = extras.get("adjoint")
+            line["relaxed"] = extras.get("relaxed")
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -59,7 +59,10 @@ typedef struct rk_plan rk_plan;
 /* Solver options.  rk_opts_default() fills the defaults given in brackets. */
 typedef struct {
     float omega;           /* relaxation of Eq. (alg) (the paper's alpha_i / uniform weight
-                              alpha of Eq. (rka_uni_weights)), in (0, 2)            [1.0] */
+                              alpha of Eq. (rka_uni_weights)), in (0, 2q) for q workers:
+                              one chain converges for (0, 2); the averaged step of RKA
+                              takes weights up to alpha* of Eq. (best_alpha) < 2q
+                              (rk_alpha_star)                                        [1.0] */
     int64_t check_every;   /* rounds between convergence checks; 0 = never          [1]   */
     double tol;            /* stop after the first checked round with metric < tol  [0]   */
     int criterion;         /* 0 none; 1 ||x - x_ref|| / ||x_ref|| (needs x_ref)    [0]   */
@@ -185,14 +188,14 @@ typedef struct {
  * hosted by another runtime that owns every device allocation and gives it only a
  * stream, or a real-time loop that forbids allocation after start-up.  The paper has
  * no counterpart; it is the same solve as rkab_solve (same kernel, same results) with
- * its scratch -- the run-state header, the q x n worker displacements and the
- * averaged iterate -- in one file-scope device array of RK_NOALLOC_SCRATCH_BYTES
+ * its scratch -- the run-state header, the q x n worker displacements, the
+ * averaged iterate and the per-worker check partials -- in one file-scope device array of RK_NOALLOC_SCRATCH_BYTES
  * (8 MiB) instead of a caller workspace, so it allocates nothing.
  *   plan, b, x0, x, q, alpha, rounds, seed, opts   as for rkab_solve
  *   result   where the outcome is written when the solve ends (stream-ordered): any
  *            address cudaMemcpyAsync accepts (device or pinned host); NULL to skip
  * Returns RK_ETOOLARGE when rk_solve_workspace_bytes(plan, q) exceeds the array
- * (about (q + 1) * ceil(n / 4) * 16 bytes; q + 1 <= 209 at n = 10000), before any device
+ * (about (q + 1) * ceil(n / 4) * 16 + 256 q bytes; q <= 207 at n = 10000), before any device
  * work.  Every GPU that loads the library holds the array until the process exits.
  * The first call on a device looks up the array's device address with that device
  * current; make that first call before any stream capture.  All calls on a device
@@ -308,6 +311,36 @@ size_t rk_residual_workspace_bytes(int64_t m, int64_t n);
 int rk_residual(const float *A, int64_t m, int64_t n, int64_t lda, const float *b,
                 const float *x, double *r, double *norms_out, int want_atr, void *workspace,
                 size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Optimal uniform weight of RKA (Section 2.3.1, Eq. (best_alpha)) for a      */
+/* consistent system, from s_min = sigma_min^2 / ||A||_F^2 and               */
+/* s_max = sigma_max^2 / ||A||_F^2:                                          */
+/*   alpha* = q / (1 + (q-1) s_min)                 if s_max - s_min <= 1/(q-1) */
+/*   alpha* = 2q / (1 + (q-1)(s_min + s_max))       otherwise                 */
+/* (q = 1 gives 1).  RKA with weight alpha* is rka_solve with               */
+/* opts->omega = alpha*.                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. (best_alpha); returns 0 for q < 1 or s_min, s_max outside [0, 1]. */
+double rk_alpha_star(int q, double s_min, double s_max);
+
+/* Bytes of device workspace rk_spectrum needs for k Lanczos steps. */
+size_t rk_spectrum_workspace_bytes(int64_t m, int64_t n, int k);
+
+/* Estimates of the extreme eigenvalues of A^T A (sigma_min^2, sigma_max^2) and ||A||_F^2
+ * for device float32 A (m x n, lda; 16-byte aligned rows): k steps (1 <= k <= 512, at most
+ * n used) of the symmetric Lanczos process on A^T A from a start vector drawn with
+ * Philox4x32-10 (key = seed), with full reorthogonalisation in float64; each step applies
+ * A^T A as two passes over A.  The end eigenvalues of the k x k tridiagonal matrix
+ * satisfy lambda_min <= out[0] and out[1] <= lambda_max up to rounding (equality once the
+ * process spans the space, e.g. k >= n).
+ *   out   host, 3 doubles <- [lambda_min estimate, lambda_max estimate, ||A||_F^2]
+ *   steps_done  host (may be NULL) <- Lanczos steps taken (fewer than k on breakdown)
+ *   workspace   device, >= rk_spectrum_workspace_bytes(m, n, k), 256-byte aligned
+ * Synchronous: waits for `stream` once per step. */
+int rk_spectrum(const float *A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed,
+                void *workspace, size_t ws_bytes, void *stream, double *out, int *steps_done);
 
 /* Name of an error code. */
 const char *rk_strerror(int code);

@@ -378,3 +378,27 @@ def cgls(A, b, x0=None, tol=1e-14, maxiter=10000):
         p = s + (gnew / gamma) * p
         gamma = gnew
     return x
+
+
+# --------------------------------------------------------------------------
+# Optimal uniform weight of RKA (Eq. (best_alpha)) and the spectrum it needs
+# --------------------------------------------------------------------------
+def spectrum(A):
+    """(sigma_min^2, sigma_max^2, ||A||_F^2) of A in FP64: singular values by LAPACK's
+    SVD (numpy), the Frobenius norm as the plain sum of squares."""
+    A64 = np.asarray(A, np.float64)
+    sv = np.linalg.svd(A64, compute_uv=False)
+    return float(sv[-1] ** 2), float(sv[0] ** 2), float(np.sum(A64 * A64))
+
+
+def alpha_star(q, s_min, s_max):
+    """Eq. (best_alpha): the optimal uniform row weight alpha of RKA (Eq. (rka_eq) with
+    w_i = alpha) for a consistent system, from s_min = sigma_min^2 / ||A||_F^2 and
+    s_max = sigma_max^2 / ||A||_F^2.  The first branch holds when the spread
+    s_max - s_min is at most 1 / (q - 1) (always for q = 1, where it gives 1)."""
+    q = int(q)
+    if q < 1:
+        raise ValueError("q >= 1")
+    if q == 1 or s_max - s_min <= 1.0 / (q - 1):
+        return q / (1.0 + (q - 1) * s_min)
+    return 2.0 * q / (1.0 + (q - 1) * (s_min + s_max))

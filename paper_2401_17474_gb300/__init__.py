@@ -14,9 +14,12 @@ from .api import (  # noqa: F401
     Residual,
     RkError,
     Solver,
+    Spectrum,
     aligned_rows,
+    alpha_star,
     launch_count,
     make_opts,
+    optimal_weight,
     quantize,
     rank2,
     rk_residual,
@@ -26,5 +29,6 @@ from .api import (  # noqa: F401
     rkab_refine,
     rkab_lstsq,
     rkab_solve,
+    spectrum,
     transpose,
 )

@@ -88,6 +88,11 @@ _SIG = {
     "rk_residual_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     "rk_residual": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _V, _V,
                                    _V, _V, ctypes.c_int, _V, ctypes.c_size_t, _V]),
+    "rk_alpha_star": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    "rk_spectrum_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int]),
+    "rk_spectrum": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                   ctypes.c_uint64, _V, ctypes.c_size_t, _V,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "rk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "rk_launch_count": (ctypes.c_uint64, []),
 }

@@ -305,6 +305,56 @@ def rk_residual(A: torch.Tensor, b, x, want_atr=True, stream=None):
     return r, norms
 
 
+# --------------------------------------------------------------------------
+# Optimal uniform weight of RKA (Eq. (best_alpha))
+# --------------------------------------------------------------------------
+def alpha_star(q: int, s_min: float, s_max: float) -> float:
+    """Eq. (best_alpha): optimal uniform weight of RKA with q workers."""
+    a = float(_lib.load().rk_alpha_star(int(q), float(s_min), float(s_max)))
+    if a <= 0.0:
+        raise RkError(_lib.RK_EINVAL, "rk_alpha_star")
+    return a
+
+
+@dataclass
+class Spectrum:
+    lambda_min: float    # estimate of sigma_min(A)^2 (from above)
+    lambda_max: float    # estimate of sigma_max(A)^2 (from below)
+    fro2: float          # ||A||_F^2
+    steps: int           # Lanczos steps taken
+
+    @property
+    def s_min(self) -> float:
+        return self.lambda_min / self.fro2
+
+    @property
+    def s_max(self) -> float:
+        return self.lambda_max / self.fro2
+
+
+def spectrum(A: torch.Tensor, k: int = 32, seed: int = 0, stream=None) -> Spectrum:
+    """Extreme eigenvalues of A^T A and ||A||_F^2 by k Lanczos steps (rk_spectrum)."""
+    if A.dtype != torch.float32 or A.stride(1) != 1 or not A.is_cuda:
+        raise ValueError("A must be a float32 CUDA matrix with unit column stride")
+    m, n = A.shape
+    lib = _lib.load()
+    nbytes = lib.rk_spectrum_workspace_bytes(m, n, int(k))
+    if nbytes == 0:
+        raise RkError(_lib.RK_EINVAL, "rk_spectrum_workspace_bytes")
+    ws = _workspace(nbytes, A.device)
+    out = (ctypes.c_double * 3)()
+    steps = ctypes.c_int(0)
+    check(lib.rk_spectrum(_ptr(A), m, n, A.stride(0), int(k), int(seed), _ptr(ws), ws.numel(),
+                          _stream(stream), out, ctypes.byref(steps)), "rk_spectrum")
+    return Spectrum(out[0], out[1], out[2], steps.value)
+
+
+def optimal_weight(A: torch.Tensor, q: int, k: int = 32, seed: int = 0, stream=None):
+    """(alpha*, Spectrum): the weight of Eq. (best_alpha) for RKA with q workers on A."""
+    sp = spectrum(A, k, seed, stream)
+    return alpha_star(q, sp.s_min, sp.s_max), sp
+
+
 def launch_count() -> int:
     """Kernel launches this process has enqueued through the library."""
     return int(_lib.load().rk_launch_count())

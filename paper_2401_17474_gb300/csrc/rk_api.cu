@@ -190,7 +190,7 @@ int rkab_solve(const rk_plan* plan, const float* b, const float* x0, float* x, i
     rk_opts o;
     rk_opts_default(&o);
     if (opts) o = *opts;
-    if (!(o.omega > 0.0f && o.omega < 2.0f) || o.check_every < 0 || o.round0 < 0 ||
+    if (!omega_ok(o.omega, q) || o.check_every < 0 || o.round0 < 0 ||
         !(o.timeout_s > 0.0) || (o.criterion == 1 && !o.x_ref) || o.criterion < 0 ||
         o.criterion > 1 || !(o.lookahead == 0 || o.lookahead == 1 || o.lookahead == 2 ||
                              o.lookahead == 4 || o.lookahead == 6) ||
@@ -270,7 +270,7 @@ int rkab_refine(const rk_plan* lowp, const float* A32, int64_t lda32, const floa
     rk_opts o;
     rk_opts_default(&o);
     if (opts) o = *opts;
-    if (!(o.omega > 0.0f && o.omega < 2.0f) || !(o.timeout_s > 0.0) ||
+    if (!omega_ok(o.omega, q) || !(o.timeout_s > 0.0) ||
         (o.criterion == 1 && !o.x_ref) || o.criterion < 0 || o.criterion > 1)
         return RK_EINVAL;
     if (ws_bytes < refine_ws_bytes(&lowp->p, q)) return RK_EWORKSPACE;
@@ -292,8 +292,8 @@ int rk_rank2(const float* r, const float* g, const float* y, const float* x, int
     return launch_rank2(r, g, y, x, m, n, G, ldg, static_cast<cudaStream_t>(stream));
 }
 
-static bool valid_opts(const rk_opts& o) {
-    return o.omega > 0.0f && o.omega < 2.0f && o.check_every >= 0 && o.round0 >= 0 &&
+static bool valid_opts(const rk_opts& o, int q) {
+    return omega_ok(o.omega, q) && o.check_every >= 0 && o.round0 >= 0 &&
            o.timeout_s > 0.0 && !(o.criterion == 1 && !o.x_ref) && o.criterion >= 0 &&
            o.criterion <= 1 &&
            (o.lookahead == 0 || o.lookahead == 1 || o.lookahead == 2 || o.lookahead == 4 ||
@@ -327,10 +327,31 @@ int rkab_adjoint(const rk_plan* plan_A, const rk_plan* plan_At, const float* b, 
     if (opts) oa = *opts;
     ot.criterion = 0;
     oa.criterion = 0;
-    if (!valid_opts(ot) || !valid_opts(oa)) return RK_EINVAL;
+    if (!valid_opts(ot, q) || !valid_opts(oa, q)) return RK_EINVAL;
     if (ws_bytes < adjoint_ws_bytes(&pa, &pt, q)) return RK_EWORKSPACE;
     return run_adjoint(&pa, &pt, b, x, gx, q, alpha_t, rounds_t, alpha, rounds, seed, ot, oa,
                        grad_b, grad_A, ldg, g, workspace, static_cast<cudaStream_t>(stream));
+}
+
+double rk_alpha_star(int q, double s_min, double s_max) {
+    if (q < 1 || !(s_min >= 0.0 && s_min <= 1.0) || !(s_max >= 0.0 && s_max <= 1.0)) return 0.0;
+    if (q == 1 || s_max - s_min <= 1.0 / (double)(q - 1)) return (double)q / (1.0 + (q - 1) * s_min);
+    return 2.0 * q / (1.0 + (q - 1) * (s_min + s_max));
+}
+
+size_t rk_spectrum_workspace_bytes(int64_t m, int64_t n, int k) {
+    if (m < 1 || n < 1 || k < 1 || k > 512) return 0;
+    return spectrum_ws_bytes(m, n, (int)(k < n ? k : n));
+}
+
+int rk_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed,
+                void* workspace, size_t ws_bytes, void* stream, double* out, int* steps_done) {
+    if (!A || !workspace || !out || m < 1 || n < 1 || lda < n || k < 1 || k > 512) return RK_EINVAL;
+    if (!aligned16(A) || (lda * 4) % 16 != 0 || ((uintptr_t)workspace & 255u) != 0) return RK_EALIGN;
+    const int kk = (int)(k < n ? k : n);
+    if (ws_bytes < spectrum_ws_bytes(m, n, kk)) return RK_EWORKSPACE;
+    return run_spectrum(A, m, n, lda, kk, seed, workspace, static_cast<cudaStream_t>(stream), out,
+                        steps_done);
 }
 
 size_t rk_residual_workspace_bytes(int64_t m, int64_t n) {

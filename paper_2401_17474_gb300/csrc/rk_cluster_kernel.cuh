@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
             for (int64_t tt = first; tt < issued; ++tt) {
                 const int st = (int)(tt % S_);
                 const uint32_t par = (uint32_t)((tt / S_) & 1);
-                wait_parity(&full[st], par, p.timeout_ns, status);
+                wait_parity(&full[st], par, drain_limit_ns(p.timeout_ns), status);
             }
         }
         __syncwarp();
@@ -377,14 +377,21 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
                 if (li < nl) reinterpret_cast<float4*>(Vg)[li] = d[k];
             }
             named_bar_sync(1, NT);
-            if (tid == 0) ctrl->flag = grid_barrier(&p.info->bar_count, &p.info->bar_gen, gridDim.x,
-                                                     status, p.timeout_ns) ? 1 : 0;
+            if (tid == 0) ctrl->flag = grid_sync(&p.info->bar_arrivals, 2ull * (unsigned long long)r,
+                                                 gridDim.x, status, p.timeout_ns) ? 1 : 0;
             named_bar_sync(1, NT);
             if (!ctrl->flag) { ok = false; break; }
-            average_slice<NT>(p, avg, r == 0);
+            // ---- convergence / divergence check over the whole averaged vector:
+            // partials of each CTA's slice while averaging, totals after the barrier ----
+            const int64_t done = r + 1;
+            const bool last = (done == p.rounds);
+            const bool check = p.check_every > 0 && (done % p.check_every == 0 || last);
+            ChkAcc ca{0.f, 0.f, 0.f};
+            average_slice<NT>(p, avg, r == 0, check ? &ca : nullptr);
             named_bar_sync(1, NT);
-            if (tid == 0) ctrl->flag = grid_barrier(&p.info->bar_count, &p.info->bar_gen, gridDim.x,
-                                                     status, p.timeout_ns) ? 1 : 0;
+            if (check) publish_check<NT>(p, ca, chk);
+            if (tid == 0) ctrl->flag = grid_sync(&p.info->bar_arrivals, 2ull * (unsigned long long)r + 1ull,
+                                                 gridDim.x, status, p.timeout_ns) ? 1 : 0;
             named_bar_sync(1, NT);
             if (!ctrl->flag) { ok = false; break; }
 #pragma unroll
@@ -394,43 +401,15 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
                 d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
 
-            // ---- convergence / divergence check over the whole averaged vector ----
-            const int64_t done = r + 1;
-            const bool last = (done == p.rounds);
-            if (p.check_every > 0 && (done % p.check_every == 0 || last)) {
-                float e2 = 0.f, r2 = 0.f, xx = 0.f;
-                for (int j = tid; j < p.n; j += NT) {
-                    const float xv = __ldcg(p.xbuf + j);
-                    xx = fmaf(xv, xv, xx);
-                    if (p.criterion == 1) {
-                        const float xr = __ldg(p.x_ref + j);
-                        const float dd = xv - xr;
-                        e2 = fmaf(dd, dd, e2);
-                        r2 = fmaf(xr, xr, r2);
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-                    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-                    xx += __shfl_xor_sync(0xffffffffu, xx, o);
-                }
-                if (lane == 0) {
-                    chk[warp] = (double)e2;
-                    chk[32 + warp] = (double)r2;
-                    chk[64 + warp] = (double)xx;
-                }
+            if (check) {
+                combine_check<NT>(p, chk);
+                const float* sh = reinterpret_cast<const float*>(chk);
+                const float XX = sh[0], E2 = sh[1], R2 = sh[2];
                 named_bar_sync(1, NT);
-                double E2 = 0.0, R2 = 0.0, XX = 0.0;
-                for (int w = 0; w < NW; ++w) {
-                    E2 += chk[w];
-                    R2 += chk[32 + w];
-                    XX += chk[64 + w];
-                }
-                named_bar_sync(1, NT);
-                double metric = -1.0;
-                if (p.criterion == 1) metric = (R2 > 0.0) ? sqrt(E2 / R2) : sqrt(E2);
-                const bool diverged = !isfinite(XX) || (p.criterion == 1 && !isfinite(metric));
+                float mf = -1.f;
+                if (p.criterion == 1) mf = (R2 > 0.f) ? sqrtf(E2 / R2) : sqrtf(E2);
+                const double metric = (double)mf;
+                const bool diverged = !isfinite(XX) || (p.criterion == 1 && !isfinite(mf));
                 if (blockIdx.x == 0 && tid == 0) {
                     p.info->rounds_done = done;
                     p.info->last_metric = metric;

@@ -69,39 +69,50 @@ __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
     return v;
 }
 
-__device__ __forceinline__ unsigned ld_acquire_gpu_u(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-// Grid-wide barrier over `nblocks` co-resident CTAs; called by ONE thread per
-// CTA.  Returns false (and leaves an error in *status) when the wait exceeds
-// timeout_ns or another CTA has already failed.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks,
-                                             int* status, uint64_t timeout_ns) {
-    __threadfence();
-    const unsigned g = ld_acquire_gpu_u(gen);
-    const unsigned arrived = atomicAdd(count, 1u);
-    if (arrived == nblocks - 1) {
-        atomicExch(count, 0u);
-        __threadfence();
-        atomicAdd(gen, 1u);
-        return ld_acquire_gpu(status) == 0;
-    }
-    const uint64_t t0 = globaltimer_ns();
-    unsigned spins = 0;
-    while (ld_acquire_gpu_u(gen) == g) {
-        if ((++spins & 63u) == 0) {
+// Limit of the wait for a CTA's own bulk copies in flight before it exits: at
+// least 2 s whatever the caller's limit, since a copy that was issued completes
+// in microseconds and the CTA must not exit while one is still writing its
+// shared memory.
+__device__ __forceinline__ uint64_t drain_limit_ns(uint64_t timeout_ns) {
+    return timeout_ns > 2000000000ull ? timeout_ns : 2000000000ull;
+}
+
+// Grid-wide barrier on a monotonic arrival counter (zero at launch): the b-th
+// barrier of every CTA (b = 0, 1, ...) completes when the counter reaches
+// (b + 1) * nblocks, so no CTA resets anything and the last arriver's single
+// atomic releases everyone.  Called by ONE thread per CTA, after a CTA-wide
+// barrier, with its own count b of barriers passed: the acq_rel atomic publishes
+// the CTA's writes (release is cumulative over what the CTA barrier ordered
+// before it) and the acquire load of the waiters orders their later reads.
+// Returns false (leaving an error in *status) when the wait exceeds timeout_ns
+// or another CTA has already failed; a CTA that failed never arrives, so the
+// others find its status in their spins.
+__device__ __forceinline__ bool grid_sync(unsigned long long* count, unsigned long long b,
+                                          unsigned nblocks, int* status, uint64_t timeout_ns) {
+    const unsigned long long target = (b + 1ull) * (unsigned long long)nblocks;
+    unsigned long long prev;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], 1;" : "=l"(prev) : "l"(count) : "memory");
+    if (prev + 1ull >= target) return true;
+    uint64_t t0 = 0;
+    for (unsigned spins = 1;; ++spins) {
+        if (ld_acquire_gpu_u64(count) >= target) return true;
+        if ((spins & 63u) == 0) {
             if (ld_acquire_gpu(status) != 0) return false;
-            if (globaltimer_ns() - t0 > timeout_ns) {
+            const uint64_t now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > timeout_ns) {
                 set_status(status, RK_ETIMEOUT);
                 return false;
             }
         }
-        __nanosleep(64);
+        if (spins > 256) __nanosleep(32);
     }
-    return ld_acquire_gpu(status) == 0;
 }
 
 // ---------------------------------------------------------------------------

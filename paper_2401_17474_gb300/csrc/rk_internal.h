@@ -59,8 +59,7 @@ struct SolveInfo {
     int pad0;
     int64_t rounds_done;
     double last_metric;
-    unsigned bar_count;
-    unsigned bar_gen;
+    unsigned long long bar_arrivals;   // monotonic arrival count of grid_sync
 };
 
 struct Plan {
@@ -96,6 +95,12 @@ int launch_residual(const float* A, int64_t m, int64_t n, int64_t lda, const flo
                     const float* x, double* r, double* norms_out, int want_atr, void* ws,
                     cudaStream_t st);
 
+int launch_normal_matvec(const float* A, int64_t m, int64_t n, int64_t lda, const float* v,
+                         double* w, void* ws, cudaStream_t st);
+size_t spectrum_ws_bytes(int64_t m, int64_t n, int k);
+int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed, void* ws,
+                 cudaStream_t st, double* out, int* steps_done);
+
 int launch_quantize(const float* A, int64_t m, int64_t n, int64_t lda, rk_dtype dt, void* out,
                     int64_t ldo, float* row_scale, cudaStream_t st);
 size_t refine_ws_bytes(const Plan* pl, int q);
@@ -117,6 +122,14 @@ int run_adjoint(const Plan* pa, const Plan* pt, const float* b, const float* x, 
 void count_launch(int k = 1);
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Relaxation / uniform row weight of Eqs. (alg) and (rka_eq): positive and below
+// 2q.  A single chain (q = 1) converges for omega in (0, 2); the averaged step of
+// q projections from one point tolerates weights up to the optimum of
+// Eq. (best_alpha), which lies in (0, 2q).
+inline bool omega_ok(float omega, int q) {
+    return omega > 0.0f && omega < 2.0f * (float)(q < 1 ? 1 : q);
+}
 
 }  // namespace rk
 

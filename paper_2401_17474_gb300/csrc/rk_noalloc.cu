@@ -62,7 +62,7 @@ extern "C" int rkab_solve_noalloc(const rk_plan* plan, const float* b, const flo
     rk_opts o;
     rk_opts_default(&o);
     if (opts) o = *opts;
-    if (!(o.omega > 0.0f && o.omega < 2.0f) || o.check_every < 0 || o.round0 < 0 ||
+    if (!omega_ok(o.omega, q) || o.check_every < 0 || o.round0 < 0 ||
         !(o.timeout_s > 0.0) || (o.criterion == 1 && !o.x_ref) || o.criterion < 0 ||
         o.criterion > 1)
         return RK_EINVAL;

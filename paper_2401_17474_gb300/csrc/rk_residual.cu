@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kResThreads) residual_rows_kernel(
         double acc = (double)hi + (double)lo;
 #pragma unroll
         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        const double ri = (double)__ldg(b + i) - acc;
+        const double ri = (b ? (double)__ldg(b + i) : 0.0) - acc;   // no b: r = -A x
         if (lane == 0) {
             r[i] = ri;
             rr = fma(ri, ri, rr);
@@ -99,7 +99,23 @@ __global__ void __launch_bounds__(kResThreads) residual_rows_kernel(
     }
 }
 
-// CTA (column tile, row chunk): partial (A^T r)_j over the chunk's rows, float64.
+// (hi, lo) += a (rh + rl) for a float32 a and a float64 r split into float32
+// rh = fl(r), rl = fl(r - rh): a rh = p + e exactly, a rl is kept rounded (its
+// error is below 2^-48 |a r|), and the sum goes through TwoSum as in df_acc.
+__device__ __forceinline__ void df_acc_split(float& hi, float& lo, float a, float rh, float rl) {
+    const float p = __fmul_rn(a, rh);
+    const float e = fmaf(a, rh, -p);
+    const float t = fmaf(a, rl, e);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, t));
+}
+
+// CTA (column tile, row chunk): partial (A^T r)_j over the chunk's rows, one
+// float4 of columns per thread, accumulated in compensated float32 pairs (about
+// 2^-46 relative to sum_i |a_ij r_i|) and written as float64.
 __global__ void __launch_bounds__(kResThreads) residual_atr_kernel(
     const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, const double* __restrict__ r,
     int chunks, double* __restrict__ atr_part) {
@@ -110,28 +126,31 @@ __global__ void __launch_bounds__(kResThreads) residual_atr_kernel(
     const int64_t i1 = min(m, i0 + rows_per);
     const int64_t j0 = ctile * kAtrCols + (int64_t)threadIdx.x * 4;
     if (j0 >= n) return;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f, l3 = 0.f;
     const bool full4 = (j0 + 3 < n);
+#pragma unroll 4
     for (int64_t i = i0; i < i1; ++i) {
         const double ri = __ldg(r + i);
+        const float rh = (float)ri;
+        const float rl = (float)(ri - (double)rh);
         const float* a = A + i * lda + j0;
         if (full4) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(a));
-            a0 = fma(ri, (double)v.x, a0);
-            a1 = fma(ri, (double)v.y, a1);
-            a2 = fma(ri, (double)v.z, a2);
-            a3 = fma(ri, (double)v.w, a3);
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(a));
+            df_acc_split(h0, l0, v.x, rh, rl);
+            df_acc_split(h1, l1, v.y, rh, rl);
+            df_acc_split(h2, l2, v.z, rh, rl);
+            df_acc_split(h3, l3, v.w, rh, rl);
         } else {
-            a0 = fma(ri, (double)__ldg(a), a0);
-            if (j0 + 1 < n) a1 = fma(ri, (double)__ldg(a + 1), a1);
-            if (j0 + 2 < n) a2 = fma(ri, (double)__ldg(a + 2), a2);
+            df_acc_split(h0, l0, __ldg(a), rh, rl);
+            if (j0 + 1 < n) df_acc_split(h1, l1, __ldg(a + 1), rh, rl);
+            if (j0 + 2 < n) df_acc_split(h2, l2, __ldg(a + 2), rh, rl);
         }
     }
     double* out = atr_part + (size_t)chunk * (size_t)n + j0;
-    out[0] = a0;
-    if (j0 + 1 < n) out[1] = a1;
-    if (j0 + 2 < n) out[2] = a2;
-    if (j0 + 3 < n) out[3] = a3;
+    out[0] = (double)h0 + (double)l0;
+    if (j0 + 1 < n) out[1] = (double)h1 + (double)l1;
+    if (j0 + 2 < n) out[2] = (double)h2 + (double)l2;
+    if (j0 + 3 < n) out[3] = (double)h3 + (double)l3;
 }
 
 // One block: norms[0] = sqrt(sum of rr partials), norms[1] = ||A^T r|| from the chunk partials.
@@ -196,6 +215,37 @@ int launch_residual(const float* A, int64_t m, int64_t n, int64_t lda, const flo
     }
     residual_finish_kernel<<<1, kResThreads, 0, st>>>(w.rr_part, nb, want_atr ? w.atr_part : nullptr,
                                                       chunks, n, norms);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
+}
+
+// w_j = -sum_c part[c][j] (chunks in ascending order): with r = -A v this is A^T A v.
+__global__ void __launch_bounds__(kResThreads) gather_neg_kernel(const double* __restrict__ part,
+                                                                  int chunks, int64_t n,
+                                                                  double* __restrict__ w) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double c = 0.0;
+        for (int k = 0; k < chunks; ++k) c += part[(size_t)k * (size_t)n + j];
+        w[j] = -c;
+    }
+}
+
+// w = A^T A v for float32 A and v: r = -A v by the row kernel (no right-hand side),
+// then the A^T r pass and the fixed-order sum of its row-chunk partials.  Two
+// passes over A; the workspace is that of launch_residual.
+int launch_normal_matvec(const float* A, int64_t m, int64_t n, int64_t lda, const float* v,
+                         double* w, void* ws, cudaStream_t st) {
+    ResWs rw = carve(ws, m, n);
+    const int nb = res_blocks(m);
+    residual_rows_kernel<<<nb, kResThreads, 0, st>>>(A, m, n, lda, nullptr, v, rw.r, rw.rr_part);
+    count_launch();
+    const int chunks = atr_chunks(m, n);
+    dim3 grid((unsigned)((n + kAtrCols - 1) / kAtrCols), (unsigned)chunks);
+    residual_atr_kernel<<<grid, kResThreads, 0, st>>>(A, m, n, lda, rw.r, chunks, rw.atr_part);
+    count_launch();
+    const int64_t gb = (n + kResThreads - 1) / kResThreads;
+    gather_neg_kernel<<<(unsigned)(gb < 1024 ? gb : 1024), kResThreads, 0, st>>>(rw.atr_part, chunks, n, w);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
 }

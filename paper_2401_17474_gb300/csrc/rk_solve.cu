@@ -89,21 +89,14 @@ static int launch_cluster_solve(const SolveArgs& a, const KParams& base, int C, 
         }
     }
     if (!var) return RK_EINVAL;
-    const size_t smem = (size_t)S * stride + cluster_ctrl_bytes(S, nt);
-    CParams cp;
-    cp.k = base;
-    cp.k.stages = S;
-    cp.k.stage_stride = stride;
-    cp.k.row_bytes = 0;   // per-CTA copy sizes are computed in the kernel
-    cp.chunk = chunk;
-    if (cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)S * stride + cluster_ctrl_bytes(S, nt))) != cudaSuccess)
         return RK_ECUDA;
     if (C > 8 && cudaFuncSetAttribute(var->fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
         return RK_ECUDA;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(a.q * C));
     cfg.blockDim = dim3((unsigned)(nt + 32));
-    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -112,13 +105,26 @@ static int launch_cluster_solve(const SolveArgs& a, const KParams& base, int C, 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // the grid barrier needs every CTA resident at once: refuse what does not fit
+    // The grid barrier needs every CTA resident at once.  A deep ring can leave
+    // one CTA per SM, and a GPC then holds fewer whole clusters: shorten the
+    // ring (down to two groups) until the q clusters fit, else refuse.
     int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, (const void*)var->fn, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return RK_ECUDA;
+    for (;;) {
+        cfg.dynamicSmemBytes = (size_t)S * stride + cluster_ctrl_bytes(S, nt);
+        if (cudaOccupancyMaxActiveClusters(&clusters, (const void*)var->fn, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            return RK_ECUDA;
+        }
+        if (clusters >= a.q || S <= 2 * var->w) break;
+        --S;
     }
     if (clusters < a.q) return RK_ENOTCORESIDENT;
+    CParams cp;
+    cp.k = base;
+    cp.k.stages = S;
+    cp.k.stage_stride = stride;
+    cp.k.row_bytes = 0;   // per-CTA copy sizes are computed in the kernel
+    cp.chunk = chunk;
     if (cudaLaunchKernelEx(&cfg, var->fn, cp) != cudaSuccess) return RK_ECUDA;
     count_launch();
     return RK_OK;
@@ -142,6 +148,7 @@ static KParams base_params(const SolveArgs& a) {
     p.V = a.V;
     p.ldv = a.ldv;
     p.xbuf = a.V + (size_t)a.q * (size_t)a.ldv;
+    p.chkpart = a.V + (size_t)(a.q + 1) * (size_t)a.ldv;
     p.q = a.q;
     p.alpha = a.alpha;
     p.rounds = a.rounds;
@@ -231,7 +238,10 @@ int launch_sample_indices(const Plan* plan, uint64_t seed, uint32_t worker, uint
 size_t solve_ws_bytes(const Plan* plan, int q) {
     const int64_t n4 = (plan->n + 3) / 4;
     const int64_t ldv = n4 * 4;
-    return align256(sizeof(SolveInfo)) + align256((size_t)(q + 1) * (size_t)ldv * sizeof(float));
+    // status | V (q x ldv) and the average (ldv) | per-CTA check partials (a float4
+    // for each of up to kClusterMax CTAs per worker)
+    return align256(sizeof(SolveInfo)) + align256((size_t)(q + 1) * (size_t)ldv * sizeof(float) +
+                                                  (size_t)q * kClusterMax * 4 * sizeof(float));
 }
 
 }  // namespace rk

@@ -65,6 +65,7 @@ struct KParams {
     float* xbuf;            // n4 float4, the average (workspace)
     float* V;               // q x ldv
     int64_t ldv;
+    float* chkpart;         // gridDim.x float4: per-CTA check partials of its x slice
     int q;
     int64_t alpha;
     int64_t rounds;
@@ -232,7 +233,7 @@ __device__ void producer_loop(const KParams& p, uint8_t* stages, uint64_t* full,
         for (int64_t tt = first; tt < issued; ++tt) {
             const int st = (int)(tt % S);
             const uint32_t par = (uint32_t)((tt / S) & 1);
-            wait_parity(&full[st], par, p.timeout_ns, status);
+            wait_parity(&full[st], par, drain_limit_ns(p.timeout_ns), status);
         }
     }
     __syncwarp();
@@ -249,13 +250,55 @@ __device__ __forceinline__ float4 load_x_old(const KParams& p, int c, bool first
     return t;
 }
 
-__device__ __forceinline__ void store_x(const KParams& p, int c, float4 xm) {
+// Partial sums of the convergence check over the columns a thread stores:
+// ||x||^2 (divergence), and for criterion 1 ||x - x_ref||^2 and ||x_ref||^2.
+// Float32 sums over a few elements each, combined by fixed-order trees: the
+// check decides a relative error of 1e-6 or more, far above their rounding.
+struct ChkAcc {
+    float xx, e2, r2;
+};
+
+__device__ __forceinline__ void store_x(const KParams& p, int c, float4 xm, ChkAcc* acc) {
     reinterpret_cast<float4*>(p.xbuf)[c] = xm;
     const int j = c * 4;
     p.x[j] = xm.x;
     if (j + 1 < p.n) p.x[j + 1] = xm.y;
     if (j + 2 < p.n) p.x[j + 2] = xm.z;
     if (j + 3 < p.n) p.x[j + 3] = xm.w;
+    if (acc) {
+        const float vv[4] = {xm.x, xm.y, xm.z, xm.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (j + e < p.n) {
+                acc->xx = fmaf(vv[e], vv[e], acc->xx);
+                if (p.criterion == 1) {
+                    const float xr = __ldg(p.x_ref + j + e);
+                    const float dd = vv[e] - xr;
+                    acc->e2 = fmaf(dd, dd, acc->e2);
+                    acc->r2 = fmaf(xr, xr, acc->r2);
+                }
+            }
+        }
+    }
+}
+
+// Sum of rows [ga, gb) of column c of V (float4), in ascending gamma, with the
+// loads issued in batches of B independent L2 reads.
+template <int B>
+__device__ __forceinline__ float4 sum_column(const KParams& p, int c, int ga, int gb) {
+    const float* col = p.V + (size_t)c * 4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int g0 = ga; g0 < gb; g0 += B) {
+        float4 w[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+            w[u] = (g0 + u < gb) ? ldcg4(col + (size_t)(g0 + u) * (size_t)p.ldv) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            acc.x += w[u].x; acc.y += w[u].y; acc.z += w[u].z; acc.w += w[u].w;
+        }
+    }
+    return acc;
 }
 
 // x <- x + (1/q) sum_gamma d_gamma (d_gamma = V[gamma]) for this CTA's
@@ -264,9 +307,10 @@ __device__ __forceinline__ void store_x(const KParams& p, int c, float4 xm) {
 // When the slice is narrower than the CTA, the workers are split into
 // `groups` contiguous ranges, each summed in ascending gamma by one thread, and
 // the group sums are added in ascending group order: a fixed two-level order,
-// the same on every run.
+// the same on every run.  With chk, the thread's check partials of the stored
+// columns are accumulated.
 template <int NT>
-__device__ __forceinline__ void average_slice(const KParams& p, float4* avg, bool first) {
+__device__ __forceinline__ void average_slice(const KParams& p, float4* avg, bool first, ChkAcc* chk) {
     const int tid = threadIdx.x;
     const int n4 = p.n4;
     const int G = gridDim.x;
@@ -274,19 +318,16 @@ __device__ __forceinline__ void average_slice(const KParams& p, float4* avg, boo
     const int c0 = blockIdx.x * cols;
     const int c1 = min(n4, c0 + cols);
     const int nc = c1 - c0;
-    const float qf = (float)p.q;
+    const float rq = 1.0f / (float)p.q;
+    // loads in flight per thread: fewer where 512 consumers share the registers
+    constexpr int kAvgBatch = NT >= 512 ? 8 : 16;
     if (nc <= 0) return;
     if (nc >= NT) {
         for (int c = c0 + tid; c < c1; c += NT) {
-            float4 acc = ldcg4(p.V + (size_t)c * 4);
-#pragma unroll 8
-            for (int g = 1; g < p.q; ++g) {
-                const float4 w = ldcg4(p.V + (size_t)g * (size_t)p.ldv + (size_t)c * 4);
-                acc.x += w.x; acc.y += w.y; acc.z += w.z; acc.w += w.w;
-            }
             const float4 xo = load_x_old(p, c, first);
-            store_x(p, c, make_float4(xo.x + acc.x / qf, xo.y + acc.y / qf, xo.z + acc.z / qf,
-                                      xo.w + acc.w / qf));
+            const float4 acc = sum_column<kAvgBatch>(p, c, 0, p.q);
+            store_x(p, c, make_float4(fmaf(acc.x, rq, xo.x), fmaf(acc.y, rq, xo.y), fmaf(acc.z, rq, xo.z),
+                                      fmaf(acc.w, rq, xo.w)), chk);
         }
         return;
     }
@@ -294,14 +335,11 @@ __device__ __forceinline__ void average_slice(const KParams& p, float4* avg, boo
     if (groups > p.q) groups = p.q;
     const int per = (p.q + groups - 1) / groups;
     const int cl = tid % nc, g = tid / nc;
+    float4 xo = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < nc) xo = load_x_old(p, c0 + tid, first);
     if (g < groups) {
         const int ga = g * per, gb = min(p.q, ga + per);
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int gg = ga; gg < gb; ++gg) {
-            const float4 w = ldcg4(p.V + (size_t)gg * (size_t)p.ldv + (size_t)(c0 + cl) * 4);
-            acc.x += w.x; acc.y += w.y; acc.z += w.z; acc.w += w.w;
-        }
-        avg[g * nc + cl] = acc;
+        avg[g * nc + cl] = sum_column<kAvgBatch>(p, c0 + cl, ga, gb);
     }
     named_bar_sync(1, NT);
     if (tid < nc) {
@@ -310,11 +348,84 @@ __device__ __forceinline__ void average_slice(const KParams& p, float4* avg, boo
             const float4 w = avg[gg * nc + tid];
             acc.x += w.x; acc.y += w.y; acc.z += w.z; acc.w += w.w;
         }
-        const int c = c0 + tid;
-        const float4 xo = load_x_old(p, c, first);
-        store_x(p, c, make_float4(xo.x + acc.x / qf, xo.y + acc.y / qf, xo.z + acc.z / qf,
-                                  xo.w + acc.w / qf));
+        store_x(p, c0 + tid, make_float4(fmaf(acc.x, rq, xo.x), fmaf(acc.y, rq, xo.y), fmaf(acc.z, rq, xo.z),
+                                         fmaf(acc.w, rq, xo.w)), chk);
     }
+}
+
+// CTA sum of the threads' check partials in a fixed order (warp butterfly, then
+// warps in ascending order), published by thread 0 as this CTA's entry of
+// p.chkpart before the grid barrier that follows.
+template <int NT>
+__device__ __forceinline__ void publish_check(const KParams& p, ChkAcc a, double* chk) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* sh = reinterpret_cast<float*>(chk);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a.xx += __shfl_xor_sync(0xffffffffu, a.xx, o);
+        a.e2 += __shfl_xor_sync(0xffffffffu, a.e2, o);
+        a.r2 += __shfl_xor_sync(0xffffffffu, a.r2, o);
+    }
+    if (lane == 0) {
+        sh[warp] = a.xx;
+        sh[32 + warp] = a.e2;
+        sh[64 + warp] = a.r2;
+    }
+    named_bar_sync(1, NT);
+    if (threadIdx.x == 0) {
+        float xx = 0.f, e2 = 0.f, r2 = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            xx += sh[w];
+            e2 += sh[32 + w];
+            r2 += sh[64 + w];
+        }
+        reinterpret_cast<float4*>(p.chkpart)[blockIdx.x] = make_float4(xx, e2, r2, 0.f);
+    }
+}
+
+// Totals of all CTAs' check partials, summed by warp 0 in a fixed order (lane l
+// takes CTAs l, l + 32, ... in ascending order, then a butterfly): every CTA
+// computes the same values from the same data.  Result in chk[0..2] for the
+// whole CTA after the closing barrier.
+template <int NT>
+__device__ __forceinline__ void combine_check(const KParams& p, double* chk) {
+    if ((threadIdx.x >> 5) == 0) {
+        const int lane = threadIdx.x & 31;
+        const int G = (int)gridDim.x;
+        float4 w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int g = lane + 32 * u;
+            w[u] = g < G ? __ldcg(reinterpret_cast<const float4*>(p.chkpart) + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float xx = 0.f, e2 = 0.f, r2 = 0.f;
+        for (int u = 0; u < 8; ++u) {
+            xx += w[u].x;
+            e2 += w[u].y;
+            r2 += w[u].z;
+        }
+        for (int g = lane + 256; g < G; g += 32) {   // grids beyond 256 CTAs
+            const float4 t = __ldcg(reinterpret_cast<const float4*>(p.chkpart) + g);
+            xx += t.x;
+            e2 += t.y;
+            r2 += t.z;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            xx += __shfl_xor_sync(0xffffffffu, xx, o);
+            e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+            r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+        }
+        if (lane == 0) {
+            float* sh = reinterpret_cast<float*>(chk);
+            sh[0] = xx;
+            sh[1] = e2;
+            sh[2] = r2;
+        }
+    }
+    named_bar_sync(1, NT);
 }
 
 // Shared memory after the stages: avg[NT] float4, full[S] + empty[S] mbarriers,
@@ -568,7 +679,9 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
             }
 #undef RK_FUSED_SLICE
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
+            // a stage whose copy this warp did not see land is never released: the
+            // producer must not refill it while that copy may still be writing
+            if (lane == 0 && got) mbar_arrive(&empty[s]);
             float part = (p01.x + p01.y) + (p23.x + p23.y);
 #pragma unroll
             for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -669,14 +782,22 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
             if (idx < n4) reinterpret_cast<float4*>(Vg)[idx] = d[k];
         }
         named_bar_sync(1, NT);
-        if (tid == 0) ctrl->flag = grid_barrier(&p.info->bar_count, &p.info->bar_gen, gridDim.x,
-                                                 status, p.timeout_ns) ? 1 : 0;
+        if (tid == 0) ctrl->flag = grid_sync(&p.info->bar_arrivals, 2ull * (unsigned long long)r, gridDim.x,
+                                             status, p.timeout_ns) ? 1 : 0;
         named_bar_sync(1, NT);
         if (!ctrl->flag) { ok = false; break; }
-        average_slice<NT>(p, avg, r == 0);
+        // ---- convergence / divergence check (identical in every CTA): each CTA
+        // sums its own slice of the new x while averaging; the totals are formed
+        // after the barrier from all CTAs' partials ----
+        const int64_t done = r + 1;
+        const bool last = (done == p.rounds);
+        const bool check = p.check_every > 0 && (done % p.check_every == 0 || last);
+        ChkAcc ca{0.f, 0.f, 0.f};
+        average_slice<NT>(p, avg, r == 0, check ? &ca : nullptr);
         named_bar_sync(1, NT);
-        if (tid == 0) ctrl->flag = grid_barrier(&p.info->bar_count, &p.info->bar_gen, gridDim.x,
-                                                 status, p.timeout_ns) ? 1 : 0;
+        if (check) publish_check<NT>(p, ca, chk);
+        if (tid == 0) ctrl->flag = grid_sync(&p.info->bar_arrivals, 2ull * (unsigned long long)r + 1ull,
+                                             gridDim.x, status, p.timeout_ns) ? 1 : 0;
         named_bar_sync(1, NT);
         if (!ctrl->flag) { ok = false; break; }
 #pragma unroll
@@ -686,56 +807,17 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
             d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
 
-        // ---- convergence / divergence check (identical in every CTA) ----
-        const int64_t done = r + 1;
-        const bool last = (done == p.rounds);
-        if (p.check_every > 0 && (done % p.check_every == 0 || last)) {
-            float e2 = 0.f, r2 = 0.f, xx = 0.f;
-#pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-                const int idx = tid + k * NT;
-                if (idx < n4) {
-                    xx = fmaf(v[k].x, v[k].x, xx);
-                    xx = fmaf(v[k].y, v[k].y, xx);
-                    xx = fmaf(v[k].z, v[k].z, xx);
-                    xx = fmaf(v[k].w, v[k].w, xx);
-                    if (p.criterion == 1) {
-                        const int j0 = idx * 4;
-                        const float vv[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            if (j0 + c < p.n) {
-                                const float xr = __ldg(p.x_ref + j0 + c);
-                                const float dd = vv[c] - xr;
-                                e2 = fmaf(dd, dd, e2);
-                                r2 = fmaf(xr, xr, r2);
-                            }
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-                r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-                xx += __shfl_xor_sync(0xffffffffu, xx, o);
-            }
-            if (lane == 0) {
-                chk[warp] = (double)e2;
-                chk[32 + warp] = (double)r2;
-                chk[64 + warp] = (double)xx;
-            }
+        if (check) {
+            combine_check<NT>(p, chk);
+            const float* sh = reinterpret_cast<const float*>(chk);
+            const float XX = sh[0], E2 = sh[1], R2 = sh[2];
             named_bar_sync(1, NT);
-            double E2 = 0.0, R2 = 0.0, XX = 0.0;
-            for (int w = 0; w < NW; ++w) {
-                E2 += chk[w];
-                R2 += chk[32 + w];
-                XX += chk[64 + w];
-            }
-            named_bar_sync(1, NT);
-            double metric = -1.0;
-            if (p.criterion == 1) metric = (R2 > 0.0) ? sqrt(E2 / R2) : sqrt(E2);
-            const bool diverged = !isfinite(XX) || (p.criterion == 1 && !isfinite(metric));
+            // float32 throughout: the float64 pipe of this device is slow, and
+            // every thread takes the decision
+            float mf = -1.f;
+            if (p.criterion == 1) mf = (R2 > 0.f) ? sqrtf(E2 / R2) : sqrtf(E2);
+            const double metric = (double)mf;
+            const bool diverged = !isfinite(XX) || (p.criterion == 1 && !isfinite(mf));
             if (gamma == 0 && tid == 0) {
                 p.info->rounds_done = done;
                 p.info->last_metric = metric;

@@ -1,0 +1,277 @@
+// rk_spectrum.cu -- the spectrum that the optimal uniform weight of RKA needs
+// (Eq. (best_alpha): s_min = sigma_min^2 / ||A||_F^2, s_max = sigma_max^2 / ||A||_F^2).
+// The extreme eigenvalues of A^T A are estimated by k steps of the symmetric
+// Lanczos process on A^T A with full reorthogonalisation (classical Gram-Schmidt
+// applied twice per step) in FP64 vectors; the operator is applied as two passes
+// over A by the residual kernels (r = -A v, then A^T r).  The end eigenvalues of
+// the k x k tridiagonal matrix are found on the host by Sturm-sequence bisection.
+// Ritz values lie inside the spectrum, so lambda_min <= est_min and
+// est_max <= lambda_max (up to rounding): with est_min, the weight of
+// Eq. (best_alpha) errs on the small side.
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "rk_common.cuh"
+#include "rk_internal.h"
+
+namespace rk {
+
+constexpr int kSpThreads = 256;
+constexpr uint32_t kSpStream = 0x5EC7u;   // Philox stream id of the start vector
+
+// v_j uniform in [-1, 1): Philox4x32-10 at counter (j, 0, stream), key = seed,
+// the top 53 bits of the first 64-bit word.
+__global__ void lanczos_start_kernel(double* __restrict__ v, int64_t n, uint64_t seed) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const U4 r = philox10(U4{(uint32_t)j, (uint32_t)((uint64_t)j >> 32), 0u, kSpStream},
+                              (uint32_t)seed, (uint32_t)(seed >> 32));
+        const uint64_t u = (uint64_t)r.x | ((uint64_t)r.y << 32);
+        v[j] = 2.0 * ((double)(u >> 11) * 0x1.0p-53) - 1.0;
+    }
+}
+
+// Fixed-order block sum of the threads' partials (power-of-two tree).
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = kSpThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// c[i] = <w, V_i> for i < cnt (one block per i).
+__global__ void __launch_bounds__(kSpThreads) multi_dot_kernel(const double* __restrict__ V, int64_t ldv,
+                                                               const double* __restrict__ w, int64_t n,
+                                                               double* __restrict__ c) {
+    __shared__ double sh[kSpThreads];
+    const double* vi = V + (size_t)blockIdx.x * (size_t)ldv;
+    double acc = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += kSpThreads) acc = fma(w[j], vi[j], acc);
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) c[blockIdx.x] = s;
+}
+
+// w_j -= sum_{i < cnt} c_i V_ij (ascending i).
+__global__ void multi_sub_kernel(double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int cnt,
+                                 const double* __restrict__ c, int64_t n) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double s = w[j];
+        for (int i = 0; i < cnt; ++i) s = fma(-c[i], V[(size_t)i * (size_t)ldv + j], s);
+        w[j] = s;
+    }
+}
+
+// out[0] = ||w||^2 (one block).
+__global__ void __launch_bounds__(kSpThreads) norm2_kernel(const double* __restrict__ w, int64_t n,
+                                                           double* __restrict__ out) {
+    __shared__ double sh[kSpThreads];
+    double acc = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += kSpThreads) acc = fma(w[j], w[j], acc);
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[0] = s;
+}
+
+// vnext = w / sqrt(nrm2[0]) (zero when w is zero), vf = float(vnext).
+__global__ void scale_kernel(const double* __restrict__ w, int64_t n, const double* __restrict__ nrm2,
+                             double* __restrict__ vnext, float* __restrict__ vf) {
+    const double nn = nrm2[0];
+    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double t = w[j] * inv;
+        vnext[j] = t;
+        vf[j] = (float)t;
+    }
+}
+
+// Per-block partial sums of a_ij^2 (one warp per row, FP64; FP32 squares are exact in FP64).
+__global__ void __launch_bounds__(kSpThreads) fro_rows_kernel(const float* __restrict__ A, int64_t m,
+                                                              int64_t n, int64_t lda,
+                                                              double* __restrict__ part) {
+    __shared__ double sh[kSpThreads];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * (kSpThreads / 32) + warp; i < m;
+         i += (int64_t)gridDim.x * (kSpThreads / 32)) {
+        const float* a = A + i * lda;
+        for (int64_t j = lane; j < n; j += 32) {
+            const double t = (double)__ldg(a + j);
+            acc = fma(t, t, acc);
+        }
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// out[0] = sum of the partials in block order.
+__global__ void sum_parts_kernel(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < nb; ++k) s += part[k];
+        out[0] = s;
+    }
+}
+
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with diagonal
+// a[0..s) and squared off-diagonals b2[1..s) (b2[i] couples i-1 and i): the
+// count of negative pivots of the LDL^T factorisation of T - x I (Sylvester's
+// law of inertia); tiny pivots are replaced by -pivmin.
+static int sturm_count(const std::vector<double>& a, const std::vector<double>& b2, double x,
+                       double pivmin) {
+    int cnt = 0;
+    double d = 1.0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        d = (a[i] - x) - (i ? b2[i] / d : 0.0);
+        if (std::fabs(d) < pivmin) d = -pivmin;
+        if (d < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// Smallest and largest eigenvalue of the tridiagonal matrix by bisection inside
+// the Gershgorin interval.
+static void tridiag_extremes(const std::vector<double>& a, const std::vector<double>& b, double* lmin,
+                             double* lmax) {
+    const size_t s = a.size();
+    std::vector<double> b2(s, 0.0);
+    double lo = INFINITY, hi = -INFINITY, scale = 0.0;
+    for (size_t i = 0; i < s; ++i) {
+        const double r = (i ? std::fabs(b[i]) : 0.0) + (i + 1 < s ? std::fabs(b[i + 1]) : 0.0);
+        lo = std::fmin(lo, a[i] - r);
+        hi = std::fmax(hi, a[i] + r);
+        if (i) b2[i] = b[i] * b[i];
+        scale = std::fmax(scale, std::fabs(a[i]) + r);
+    }
+    const double pivmin = std::fmax(scale, 1e-300) * 1e-300;
+    const int ss = (int)s;
+    auto bisect = [&](int k) {   // smallest x with count(x) >= k, i.e. the k-th eigenvalue
+        double l = lo - 1e-12 * scale, h = hi + 1e-12 * scale;
+        for (int it = 0; it < 200 && h - l > 2e-16 * std::fmax(std::fabs(l), std::fabs(h)); ++it) {
+            const double mid = 0.5 * (l + h);
+            if (sturm_count(a, b2, mid, pivmin) >= k) h = mid;
+            else l = mid;
+        }
+        return 0.5 * (l + h);
+    };
+    *lmin = bisect(1);
+    *lmax = bisect(ss);
+}
+
+struct SpecWs {
+    double* scal;    // [0] ||w||^2, [1] ||A||_F^2
+    double* c1;      // k + 1
+    double* c2;      // k + 1
+    double* V;       // (k + 1) x ldv
+    int64_t ldv;
+    double* w;       // n
+    float* vf;       // n
+    double* fpart;   // fro partials
+    void* res;       // residual workspace
+};
+
+static int fro_blocks(int64_t m) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (m + (kSpThreads / 32) - 1) / (kSpThreads / 32);
+    const int64_t cap = (int64_t)sms * 4;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+static SpecWs spec_carve(void* base, int64_t m, int64_t n, int k) {
+    uint8_t* p = static_cast<uint8_t*>(base);
+    SpecWs w;
+    w.ldv = (n + 31) / 32 * 32;
+    w.scal = reinterpret_cast<double*>(p);
+    p += 256;
+    w.c1 = reinterpret_cast<double*>(p);
+    p += align256((size_t)(k + 1) * 8);
+    w.c2 = reinterpret_cast<double*>(p);
+    p += align256((size_t)(k + 1) * 8);
+    w.V = reinterpret_cast<double*>(p);
+    p += align256((size_t)(k + 1) * (size_t)w.ldv * 8);
+    w.w = reinterpret_cast<double*>(p);
+    p += align256((size_t)n * 8);
+    w.vf = reinterpret_cast<float*>(p);
+    p += align256((size_t)n * 4);
+    w.fpart = reinterpret_cast<double*>(p);
+    p += align256((size_t)fro_blocks(m) * 8);
+    w.res = p;
+    return w;
+}
+
+size_t spectrum_ws_bytes(int64_t m, int64_t n, int k) {
+    const size_t ldv = (size_t)((n + 31) / 32 * 32);
+    return 256 + 2 * align256((size_t)(k + 1) * 8) + align256((size_t)(k + 1) * ldv * 8) +
+           align256((size_t)n * 8) + align256((size_t)n * 4) + align256((size_t)fro_blocks(m) * 8) +
+           residual_ws_bytes(m, n);
+}
+
+static int grid_for(int64_t n) {
+    const int64_t g = (n + kSpThreads - 1) / kSpThreads;
+    return (int)(g < 1 ? 1 : (g < 2048 ? g : 2048));
+}
+
+int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed, void* ws,
+                 cudaStream_t st, double* out, int* steps_done) {
+    SpecWs w = spec_carve(ws, m, n, k);
+    if (steps_done) *steps_done = 0;
+    // ||A||_F^2
+    const int fb = fro_blocks(m);
+    fro_rows_kernel<<<fb, kSpThreads, 0, st>>>(A, m, n, lda, w.fpart);
+    sum_parts_kernel<<<1, 32, 0, st>>>(w.fpart, fb, w.scal + 1);
+    count_launch(2);
+    // v_0: seeded start vector, normalised
+    lanczos_start_kernel<<<grid_for(n), kSpThreads, 0, st>>>(w.w, n, seed);
+    norm2_kernel<<<1, kSpThreads, 0, st>>>(w.w, n, w.scal);
+    scale_kernel<<<grid_for(n), kSpThreads, 0, st>>>(w.w, n, w.scal, w.V, w.vf);
+    count_launch(3);
+    if (cudaGetLastError() != cudaSuccess) return RK_ECUDA;
+
+    std::vector<double> alpha, beta(1, 0.0);   // beta[j] couples steps j-1 and j
+    double fro2 = 0.0;
+    for (int j = 0; j < k; ++j) {
+        // w = A^T A v_j
+        int rc = launch_normal_matvec(A, m, n, lda, w.vf, w.w, w.res, st);
+        if (rc != RK_OK) return rc;
+        // two passes of classical Gram-Schmidt against v_0 .. v_j
+        const int cnt = j + 1;
+        multi_dot_kernel<<<cnt, kSpThreads, 0, st>>>(w.V, w.ldv, w.w, n, w.c1);
+        multi_sub_kernel<<<grid_for(n), kSpThreads, 0, st>>>(w.w, w.V, w.ldv, cnt, w.c1, n);
+        multi_dot_kernel<<<cnt, kSpThreads, 0, st>>>(w.V, w.ldv, w.w, n, w.c2);
+        multi_sub_kernel<<<grid_for(n), kSpThreads, 0, st>>>(w.w, w.V, w.ldv, cnt, w.c2, n);
+        norm2_kernel<<<1, kSpThreads, 0, st>>>(w.w, n, w.scal);
+        scale_kernel<<<grid_for(n), kSpThreads, 0, st>>>(w.w, n, w.scal, w.V + (size_t)cnt * (size_t)w.ldv,
+                                                         w.vf);
+        count_launch(6);
+        double h[4];
+        if (cudaMemcpyAsync(&h[0], w.c1 + j, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&h[1], w.c2 + j, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&h[2], w.scal, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return RK_ECUDA;
+        fro2 = h[3];
+        if (!std::isfinite(h[0]) || !std::isfinite(h[2])) return RK_EDIVERGED;
+        alpha.push_back(h[0] + h[1]);   // <A^T A v_j, v_j> with the second pass's correction
+        const double bn = std::sqrt(h[2]);
+        if (steps_done) *steps_done = j + 1;
+        // an invariant subspace ends the process (always by j = n - 1)
+        double amax = 0.0;
+        for (double a : alpha) amax = std::fmax(amax, std::fabs(a));
+        if (!(bn > 1e-13 * amax) || j + 1 == n) break;
+        beta.push_back(bn);
+    }
+    beta.resize(alpha.size(), 0.0);
+    tridiag_extremes(alpha, beta, &out[0], &out[1]);
+    out[2] = fro2;
+    return RK_OK;
+}
+
+}  // namespace rk

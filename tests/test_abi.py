@@ -64,3 +64,23 @@ def test_host_side_queries_need_no_device(lib):
     assert L.rk_setup(ctypes.c_void_p(16), 0, None, 10, 10, 10, ctypes.c_void_p(256), 1 << 30, None,
                       ctypes.byref(h)) == _lib.RK_EALIGN      # lda*4 = 40 not a multiple of 16
     assert L.rkab_solve(None, None, None, None, 1, 1, 1, 0, None, None, 0, None) == _lib.RK_EINVAL
+
+
+def test_alpha_star_is_the_oracle_formula(lib):
+    """rk_alpha_star (host arithmetic in the library) reproduces Eq. (best_alpha) as the
+    oracle writes it, on both branches, bit for bit."""
+    import oracle
+    from paper_2401_17474_gb300 import _lib
+    L = _lib.load()
+    cases = [(1, 0.2, 0.4), (2, 5e-4, 5e-4), (4, 6.7e-4, 2e-3), (132, 4.19e-5, 1.83e-4),
+             (8, 0.01, 0.5), (64, 0.001, 0.9), (3, 0.0, 1.0)]
+    for q, s0, s1 in cases:
+        assert L.rk_alpha_star(q, s0, s1) == oracle.alpha_star(q, s0, s1), (q, s0, s1)
+    # invalid arguments give 0
+    assert L.rk_alpha_star(0, 0.1, 0.2) == 0.0
+    assert L.rk_alpha_star(4, -0.1, 0.2) == 0.0
+    assert L.rk_alpha_star(4, 0.1, 1.5) == 0.0
+    # spectrum workspace query: host only
+    assert L.rk_spectrum_workspace_bytes(1000, 100, 32) > 33 * 100 * 8
+    assert L.rk_spectrum_workspace_bytes(1000, 100, 0) == 0
+    assert L.rk_spectrum_workspace_bytes(1000, 100, 513) == 0

@@ -216,7 +216,7 @@ def test_argument_errors(rk, c1):
     with pytest.raises(rk.RkError):
         rk.rkab_solve(plan, b, q=0, alpha=1, rounds=1)
     with pytest.raises(rk.RkError):
-        rk.rkab_solve(plan, b, q=2, alpha=1, rounds=1, omega=2.0)
+        rk.rkab_solve(plan, b, q=2, alpha=1, rounds=1, omega=4.0)   # omega < 2q
     with pytest.raises(rk.RkError) as e:
         rk.rkab_solve(plan, b, q=100000, alpha=1, rounds=1)
     assert e.value.code == -3   # not co-resident: refused before launch
@@ -255,3 +255,19 @@ def test_full_size_sampled_parity(rk):
     x, info = rk.rkab_solve(plan, b, q=q, alpha=n, rounds=400, seed=0, x_ref=xs, tol=1e-6)
     assert info.status == 0 and info.last_metric < 1e-6, info
     assert _rel(x.cpu().numpy(), s.x_star.astype(np.float64)) < 1e-6
+
+
+def test_wait_limit_ends_the_solve_with_a_status(rk):
+    """Every device-side wait is bounded: with a 1 us limit the first wait for a row
+    (a cold HBM copy takes longer) runs out, the kernel winds down (copies in flight
+    drained, no stage refilled) and reports RK_ETIMEOUT; the context stays usable."""
+    A_t, b_t, xs_t = rk_inputs.gaussian_system_torch(20000, 2000, seed=4, device="cuda")
+    plan = rk.rk_setup(A_t)
+    x, info = rk.rkab_solve(plan, b_t, q=4, alpha=500, rounds=3, seed=1, check_every=0,
+                            timeout_s=1e-6, raise_on_error=False)
+    torch.cuda.synchronize()
+    assert info.status == -4, info   # RK_ETIMEOUT
+    # the same plan solves normally afterwards
+    x, info = rk.rkab_solve(plan, b_t, q=4, alpha=500, rounds=3, seed=1, check_every=0)
+    assert info.status == 0
+    assert torch.isfinite(x).all()
