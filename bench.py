@@ -65,6 +65,9 @@ def parse():
                     help="CTAs per worker of the timed solve (0/1: one CTA per worker)")
     ap.add_argument("--lookahead", type=int, default=0,
                     help="rows per look-ahead group of the timed solve (0: automatic)")
+    ap.add_argument("--omega", default="1",
+                    help="relaxation of the timed solve: a number, or 'star' for alpha* of "
+                         "Eq. (best_alpha) from the GPU spectrum estimate (computed before timing)")
     ap.add_argument("--workload", default="consistent", choices=["consistent", "lsq", "precision"],
                     help="consistent: 80000 x 10000 to 1e-6 (default); lsq: 200000 x 20000 "
                          "row-scaled inconsistent system, budget of rounds with the normal-equation "
@@ -276,23 +279,33 @@ def _timed(fn, reps=2):
     return best
 
 
-def extra_cells(rk, plan, b, xs, n, tol, max_rounds):
-    """Time to tolerance of the configurations of the benchmark's cell list and of RK."""
+def extra_cells(rk, A, plan, b, xs, n, tol, max_rounds):
+    """Time to tolerance of every cell of the benchmark's list (q in {8, 32, 132},
+    alpha in {n, n/10, 1}) with the unit weight, the alpha = 1 cells (RKA) also with
+    the optimal weight of Eq. (best_alpha), and RK and cluster workers.  A cell that
+    does not reach the tolerance within its round budget reports its last metric."""
     import torch
     x0 = torch.zeros(n, dtype=torch.float32, device=b.device)
     x = torch.empty_like(x0)
+    sp = rk.spectrum(A, k=8)
     out = {}
-    cells = [("q132_alpha_n", 132, n, 0), ("q132_alpha_n/10", 132, n // 10, 0),
-             ("q32_alpha_n", 32, n, 0), ("q8_alpha_n", 8, n, 0),
-             ("q8_alpha_n_cluster16", 8, n, 16), ("q32_alpha_n_cluster4", 32, n, 4),
-             ("rk_q1", 1, n, 0), ("rk_q1_cluster16", 1, n, 16)]
-    for name, q, alpha, C in cells:
+    cells = []
+    for q in (132, 32, 8):
+        cells += [(f"q{q}_alpha_n", q, n, 0, 1.0, max_rounds),
+                  (f"q{q}_alpha_n/10", q, n // 10, 0, 1.0, 10 * max_rounds),
+                  (f"q{q}_alpha_1_omega1", q, 1, 0, 1.0, 400000),
+                  (f"q{q}_alpha_1_omega_star", q, 1, 0, rk.alpha_star(q, sp.s_min, sp.s_max), 200000)]
+    cells += [("q8_alpha_n_cluster16", 8, n, 16, 1.0, max_rounds),
+              ("q32_alpha_n_cluster4", 32, n, 4, 1.0, max_rounds),
+              ("rk_q1", 1, n, 0, 1.0, max_rounds), ("rk_q1_cluster16", 1, n, 16, 1.0, max_rounds)]
+    for name, q, alpha, C, omega, rounds in cells:
         try:
             s = rk.Solver(plan, q)
-            o = rk.make_opts(check_every=1, tol=tol, x_ref=xs, cluster_size=C)
-            t = _timed(lambda: s.launch(b, x0, x, alpha, max_rounds * (n // alpha), 0, o))
+            o = rk.make_opts(check_every=1, tol=tol, x_ref=xs, cluster_size=C, omega=omega)
+            t = _timed(lambda: s.launch(b, x0, x, alpha, rounds, 0, o), reps=1)
             inf = s.info()
-            out[name] = {"ms": round(t, 2), "rounds": inf.rounds_done, "metric": inf.last_metric,
+            out[name] = {"ms": round(t, 2), "omega": round(omega, 4), "rounds": inf.rounds_done,
+                         "metric": inf.last_metric, "reached": bool(0 <= inf.last_metric < tol),
                          "row_proj": q * alpha * inf.rounds_done, "status": inf.status}
         except Exception as e:  # a cell that cannot run on this device is reported, not fatal
             out[name] = {"error": str(e)}
@@ -350,13 +363,13 @@ def extra_relaxed(rk, A, plan, b, xs, n, tol):
     torch.cuda.synchronize()
     out["spectrum"] = {"ms": round(e0.elapsed_time(e1), 2), "lanczos_steps": sp.steps,
                        "s_min": sp.s_min, "s_max": sp.s_max}
-    cells = [("rka_q132_alpha_star", 132, 1, rk.alpha_star(132, sp.s_min, sp.s_max), 20000),
-             ("rka_q152_alpha_star", 152, 1, rk.alpha_star(152, sp.s_min, sp.s_max), 20000),
-             ("rka_q32_alpha_star", 32, 1, rk.alpha_star(32, sp.s_min, sp.s_max), 40000),
-             ("rka_q132_omega1", 132, 1, 1.0, 400000),
-             ("rkab_q152_alpha20_omega24", 152, 20, 24.0, 4000),
-             ("rkab_q152_alpha50_omega16", 152, 50, 16.0, 2000),
-             ("rkab_q152_alpha10_omega32", 152, 10, 32.0, 6000)]
+    sms = torch.cuda.get_device_properties(b.device).multi_processor_count
+    cells = [(f"rka_q{sms}_alpha_star", sms, 1, rk.alpha_star(sms, sp.s_min, sp.s_max), 20000)]
+    for mult in (4, 16, 32, 64):
+        q = sms * mult
+        cells.append((f"rka_q{q}_alpha_star", q, 1, rk.alpha_star(q, sp.s_min, sp.s_max), 20000))
+    cells += [(f"rkab_q{sms}_alpha10_omega40", sms, 10, 40.0, 6000),
+              (f"rkab_q{sms}_alpha20_omega32", sms, 20, 32.0, 4000)]
     for name, q, alpha, omega, max_rounds in cells:
         try:
             s = rk.Solver(plan, q)
@@ -368,6 +381,12 @@ def extra_relaxed(rk, A, plan, b, xs, n, tol):
                          "row_proj": q * alpha * inf.rounds_done, "status": inf.status}
         except Exception as e:
             out[name] = {"error": str(e)}
+    ok = [(v["ms"], k) for k, v in out.items()
+          if isinstance(v, dict) and v.get("status") == 0 and 0 <= v.get("metric", -1) < tol]
+    if ok:
+        ms, k = min(ok)
+        out["best"] = {"cell": k, "solve_ms": ms, "spectrum_ms": out["spectrum"]["ms"],
+                       "solve_plus_spectrum_ms": round(ms + out["spectrum"]["ms"], 2)}
     return out
 
 
@@ -590,8 +609,12 @@ def run_ours(args):
         A_solve, scale_solve = rk.quantize(A, args.dtype)
     elem = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
     solver = rk.Solver(plan0, q)
+    if args.omega == "star":
+        omega, _ = rk.optimal_weight(A, q, k=8)
+    else:
+        omega = float(args.omega)
     opts = rk.make_opts(check_every=1, tol=args.tol, x_ref=xs, cluster_size=args.cluster,
-                        lookahead=args.lookahead)
+                        lookahead=args.lookahead, omega=omega)
 
     def step(record=None):
         if args.dtype == "f32":
@@ -662,7 +685,8 @@ def run_ours(args):
     kmean_s = sum(kern_ms) / len(kern_ms) / 1e3
     alg = algorithmic_bytes(n, q, alpha, rounds_t, elem)
     achieved = alg / kmean_s / 1e9
-    default_cfg = (m, n, q, alpha, args.dtype, args.cluster) == (80000, 10000, 132, 10000, "f32", 0)
+    default_cfg = ((m, n, q, alpha, args.dtype, args.cluster, omega) ==
+                   (80000, 10000, 132, 10000, "f32", 0, 1.0))
     traffic_pp = recorded_traffic("c2") if default_cfg else None
     traffic = None if traffic_pp is None else traffic_pp * q * alpha * rounds_t
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -695,7 +719,8 @@ def run_ours(args):
             solver.plan = pl
             solver.launch(b_d, x0, x, alpha, args.max_rounds, args.seed,
                           rk.make_opts(check_every=1, tol=args.tol, x_ref=xs_d,
-                                       cluster_size=args.cluster, lookahead=args.lookahead),
+                                       cluster_size=args.cluster, lookahead=args.lookahead,
+                                       omega=omega),
                           stream)
             x_h.copy_(x, non_blocking=True)
         e1.record(stream)
@@ -709,7 +734,7 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras and rank == 0:
-        for key, fn in (("cells", lambda: extra_cells(rk, plan0, b, xs, n, args.tol, 40)),
+        for key, fn in (("cells", lambda: extra_cells(rk, A, plan0, b, xs, n, args.tol, 40)),
                         ("precision", lambda: extra_precision(rk, A, plan0, b, xs, n, q, alpha,
                                                               args.tol)),
                         ("relaxed", lambda: extra_relaxed(rk, A, plan0, b, xs, n, args.tol)),
@@ -733,9 +758,10 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"rkab_consistent_{m}x{n}_q{q}_alpha{alpha}_{dname}"
+                                   + ("" if omega == 1.0 else f"_omega{omega:.4g}")
                                    + (f"_cluster{args.cluster}" if args.cluster > 1 else ""),
                        "m": m, "n": n, "q": q, "alpha": alpha, "tol": args.tol,
-                       "stored_rows": args.dtype, "cluster": args.cluster,
+                       "stored_rows": args.dtype, "cluster": args.cluster, "omega": omega,
                        "criterion": "||x-x*||/||x*||, checked after every average",
                        "rounds_to_tol": rounds_t, "parallelism": f"replicas{ws}",
                        "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 4 / 1e9),
@@ -749,6 +775,9 @@ def run_ours(args):
             line["precision"] = extras.get("precision")
             line["adjoint"] = extras.get("adjoint")
             line["relaxed"] = extras.get("relaxed")
+            best = (extras.get("relaxed") or {}).get("best")
+            if best:
+                line["time_to_tol_best"] = best
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -15,6 +15,7 @@ constexpr int kAtrCols = 1024;  // columns per CTA of the A^T r pass (one float4
 
 struct ResWs {
     double* r;         // m (used when the caller passes no r)
+    float2* rs;        // m: r_i split into float32 (hi, lo) for the A^T r pass
     double* rr_part;   // per-block sums of r_i^2
     double* atr_part;  // [row chunks][n]
     double* norms;     // [2] when the caller passes none
@@ -62,7 +63,8 @@ __device__ __forceinline__ void df_acc(float& hi, float& lo, float a, float x) {
 // of the device is not needed per element, so the pass runs at memory speed.
 __global__ void __launch_bounds__(kResThreads) residual_rows_kernel(
     const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, const float* __restrict__ b,
-    const float* __restrict__ x, double* __restrict__ r, double* __restrict__ rr_part) {
+    const float* __restrict__ x, double* __restrict__ r, float2* __restrict__ rs,
+    double* __restrict__ rr_part) {
     __shared__ double s_rr[kResThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n4 = n >> 2;
@@ -87,6 +89,8 @@ __global__ void __launch_bounds__(kResThreads) residual_rows_kernel(
         const double ri = (b ? (double)__ldg(b + i) : 0.0) - acc;   // no b: r = -A x
         if (lane == 0) {
             r[i] = ri;
+            const float rh = (float)ri;
+            rs[i] = make_float2(rh, (float)(ri - (double)rh));
             rr = fma(ri, ri, rr);
         }
     }
@@ -117,7 +121,7 @@ __device__ __forceinline__ void df_acc_split(float& hi, float& lo, float a, floa
 // float4 of columns per thread, accumulated in compensated float32 pairs (about
 // 2^-46 relative to sum_i |a_ij r_i|) and written as float64.
 __global__ void __launch_bounds__(kResThreads) residual_atr_kernel(
-    const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, const double* __restrict__ r,
+    const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, const float2* __restrict__ rs,
     int chunks, double* __restrict__ atr_part) {
     const int64_t ctile = blockIdx.x;
     const int chunk = blockIdx.y;
@@ -130,9 +134,8 @@ __global__ void __launch_bounds__(kResThreads) residual_atr_kernel(
     const bool full4 = (j0 + 3 < n);
 #pragma unroll 4
     for (int64_t i = i0; i < i1; ++i) {
-        const double ri = __ldg(r + i);
-        const float rh = (float)ri;
-        const float rl = (float)(ri - (double)rh);
+        const float2 rr = __ldg(rs + i);   // r_i = rh + rl, split once per row
+        const float rh = rr.x, rl = rr.y;
         const float* a = A + i * lda + j0;
         if (full4) {
             const float4 v = __ldcs(reinterpret_cast<const float4*>(a));
@@ -186,6 +189,8 @@ static ResWs carve(void* base, int64_t m, int64_t n) {
     p += 256;
     w.r = reinterpret_cast<double*>(p);
     p += align256((size_t)m * 8);
+    w.rs = reinterpret_cast<float2*>(p);
+    p += align256((size_t)m * 8);
     w.rr_part = reinterpret_cast<double*>(p);
     p += align256((size_t)res_blocks(m) * 8);
     w.atr_part = reinterpret_cast<double*>(p);
@@ -193,7 +198,7 @@ static ResWs carve(void* base, int64_t m, int64_t n) {
 }
 
 size_t residual_ws_bytes(int64_t m, int64_t n) {
-    return 256 + align256((size_t)m * 8) + align256((size_t)res_blocks(m) * 8) +
+    return 256 + 2 * align256((size_t)m * 8) + align256((size_t)res_blocks(m) * 8) +
            align256((size_t)atr_chunks(m, n) * (size_t)n * 8);
 }
 
@@ -204,13 +209,13 @@ int launch_residual(const float* A, int64_t m, int64_t n, int64_t lda, const flo
     double* rv = r ? r : w.r;
     double* norms = norms_out ? norms_out : w.norms;
     const int nb = res_blocks(m);
-    residual_rows_kernel<<<nb, kResThreads, 0, st>>>(A, m, n, lda, b, x, rv, w.rr_part);
+    residual_rows_kernel<<<nb, kResThreads, 0, st>>>(A, m, n, lda, b, x, rv, w.rs, w.rr_part);
     count_launch();
     int chunks = 0;
     if (want_atr) {
         chunks = atr_chunks(m, n);
         dim3 grid((unsigned)((n + kAtrCols - 1) / kAtrCols), (unsigned)chunks);
-        residual_atr_kernel<<<grid, kResThreads, 0, st>>>(A, m, n, lda, rv, chunks, w.atr_part);
+        residual_atr_kernel<<<grid, kResThreads, 0, st>>>(A, m, n, lda, w.rs, chunks, w.atr_part);
         count_launch();
     }
     residual_finish_kernel<<<1, kResThreads, 0, st>>>(w.rr_part, nb, want_atr ? w.atr_part : nullptr,
@@ -238,11 +243,11 @@ int launch_normal_matvec(const float* A, int64_t m, int64_t n, int64_t lda, cons
                          double* w, void* ws, cudaStream_t st) {
     ResWs rw = carve(ws, m, n);
     const int nb = res_blocks(m);
-    residual_rows_kernel<<<nb, kResThreads, 0, st>>>(A, m, n, lda, nullptr, v, rw.r, rw.rr_part);
+    residual_rows_kernel<<<nb, kResThreads, 0, st>>>(A, m, n, lda, nullptr, v, rw.r, rw.rs, rw.rr_part);
     count_launch();
     const int chunks = atr_chunks(m, n);
     dim3 grid((unsigned)((n + kAtrCols - 1) / kAtrCols), (unsigned)chunks);
-    residual_atr_kernel<<<grid, kResThreads, 0, st>>>(A, m, n, lda, rw.r, chunks, rw.atr_part);
+    residual_atr_kernel<<<grid, kResThreads, 0, st>>>(A, m, n, lda, rw.rs, chunks, rw.atr_part);
     count_launch();
     const int64_t gb = (n + kResThreads - 1) / kResThreads;
     gather_neg_kernel<<<(unsigned)(gb < 1024 ? gb : 1024), kResThreads, 0, st>>>(rw.atr_part, chunks, n, w);

@@ -29,16 +29,19 @@ __global__ void sample_indices_kernel(const uint64_t* __restrict__ thr64,
 // registers/thread, 512 + 1 only 96): 32 threads up to n = 512, 128 up to
 // n = 2560, 256 up to n = 10240, else 512 (row re-read from shared memory);
 // then the smallest instantiated slices-per-thread count that covers n.
-static const SolveVariant* pick_variant(rk_dtype dt, int n4, int w) {
+static const SolveVariant* pick_variant(rk_dtype dt, int n4, int w, int minb = 1, bool jac = false) {
     int count = 0;
     const SolveVariant* tab = dt == RK_F32 ? solve_variants_f32(&count)
                             : dt == RK_BF16 ? solve_variants_bf16(&count)
                                             : solve_variants_fp8(&count);
-    const int nt = n4 <= 32 * 4 ? 32 : (n4 <= 128 * 5 ? 128 : (n4 <= 256 * 10 ? 256 : 512));
+    int nt = n4 <= 32 * 4 ? 32 : (n4 <= 128 * 5 ? 128 : (n4 <= 256 * 10 ? 256 : 512));
+    // two workers per SM: 128 or 256 consumers, slices re-read from shared memory
+    if (minb == 2) nt = n4 <= 128 * 5 ? 128 : 256;
     const int need = (n4 + nt - 1) / nt;
     const SolveVariant* best = nullptr;
     for (int i = 0; i < count; ++i) {
-        if (tab[i].nt == nt && tab[i].w == w && tab[i].vpt >= need && (!best || tab[i].vpt < best->vpt))
+        if (tab[i].minb == minb && tab[i].jac == jac && tab[i].nt == nt && tab[i].w == w && tab[i].vpt >= need &&
+            (!best || tab[i].vpt < best->vpt))
             best = &tab[i];
     }
     return best;
@@ -149,6 +152,8 @@ static KParams base_params(const SolveArgs& a) {
     p.ldv = a.ldv;
     p.xbuf = a.V + (size_t)a.q * (size_t)a.ldv;
     p.chkpart = a.V + (size_t)(a.q + 1) * (size_t)a.ldv;
+    p.vrows = a.q;
+    p.jacobi = 0;
     p.q = a.q;
     p.alpha = a.alpha;
     p.rounds = a.rounds;
@@ -178,18 +183,56 @@ int launch_solve(const SolveArgs& a, cudaStream_t st) {
     // slices of 4 elements; the copy is rounded up to 16 bytes, which stays inside
     // the row's lda extent because lda * element size is a multiple of 16
     const uint32_t row_bytes = ((uint32_t)n4 * 4u * (uint32_t)elem_size(pl->dt) + 15u) & ~15u;
+    // More workers than SMs: the two-per-SM variants (W = 1), each CTA within half
+    // of the SM's shared memory (less the per-block reservation).
+    int sms = 0, smem_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // RKA (alpha = 1) with more workers than SMs: the q single-projection workers
+    // of a round are spread over one CTA per SM, each summing its workers'
+    // projections from the round's x (their order inside the CTA does not matter:
+    // they are independent, Eq. (rka_eq))
+    const bool jac = a.alpha == 1 && a.q > sms;
+    const int grid = jac ? sms : a.q;
+    if (a.q > sms && !jac) {
+        const SolveVariant* v2 = pick_variant(pl->dt, n4, 1, 2);
+        if (!v2 || a.q > 2 * sms) return RK_ENOTCORESIDENT;
+        const int half = smem_sm / 2 - 1024;
+        const uint32_t padded2 = (uint32_t)v2->nt * (uint32_t)v2->vpt * 4u * (uint32_t)elem_size(pl->dt);
+        const uint32_t stride2 = ((row_bytes > padded2 ? row_bytes : padded2) + 127u) & ~127u;
+        const int S2 = stages_for(stride2, v2->nt, half < smem_max ? half : smem_max);
+        if (S2 < 2) return RK_ENOTCORESIDENT;
+        const size_t smem2 = (size_t)S2 * stride2 + solve_ctrl_bytes(S2, v2->nt);
+        KParams p2 = base_params(a);
+        p2.stages = S2;
+        p2.row_bytes = row_bytes;
+        p2.stage_stride = stride2;
+        if (cudaFuncSetAttribute(v2->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) !=
+            cudaSuccess)
+            return RK_ECUDA;
+        void* args2[] = {(void*)&p2};
+        cudaError_t e2 = cudaLaunchCooperativeKernel((const void*)v2->fn, dim3((unsigned)a.q),
+                                                     dim3((unsigned)(v2->nt + 32)), args2, smem2, st);
+        if (e2 == cudaErrorCooperativeLaunchTooLarge) {
+            cudaGetLastError();
+            return RK_ENOTCORESIDENT;
+        }
+        if (e2 != cudaSuccess) return RK_ECUDA;
+        count_launch();
+        return RK_OK;
+    }
     // look-ahead groups pay off when the per-row reduction outweighs the slice
     // work (short rows); the ring must hold two groups so that the producer fills
     // one while the consumers work on the other
-    int w = a.opts.lookahead;
+    int w = jac ? 1 : a.opts.lookahead;
     const SolveVariant* var = nullptr;
     uint32_t stride = 0;
     int S = 0;
     for (int attempt = 0; attempt < 3; ++attempt) {
-        const SolveVariant* v1 = pick_variant(pl->dt, n4, 1);
+        const SolveVariant* v1 = pick_variant(pl->dt, n4, 1, 1, jac);
         if (!v1) return RK_EINVAL;
-        const int wauto = (w == 0) ? (v1->vpt <= 3 ? 4 : 1) : w;
-        var = pick_variant(pl->dt, n4, wauto);
+        const int wauto = jac ? 1 : ((w == 0) ? (v1->vpt <= 3 ? 4 : 1) : w);
+        var = pick_variant(pl->dt, n4, wauto, 1, jac);
         if (!var) var = v1;
         // stages are padded to the variant's NT * VPT slices (zeroed at kernel start)
         const uint32_t padded = (uint32_t)var->nt * (uint32_t)var->vpt * 4u * (uint32_t)elem_size(pl->dt);
@@ -206,12 +249,16 @@ int launch_solve(const SolveArgs& a, cudaStream_t st) {
     p.stages = S;
     p.row_bytes = row_bytes;
     p.stage_stride = stride;
+    if (jac) {
+        p.jacobi = 1;
+        p.vrows = grid;
+    }
 
     if (cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return RK_ECUDA;
     void* args[] = {(void*)&p};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)var->fn, dim3((unsigned)a.q),
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)var->fn, dim3((unsigned)grid),
                                                 dim3((unsigned)(var->nt + 32)), args, smem, st);
     if (e == cudaErrorCooperativeLaunchTooLarge) {
         cudaGetLastError();

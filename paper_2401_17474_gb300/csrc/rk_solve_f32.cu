@@ -3,7 +3,9 @@
 
 namespace rk {
 
-#define V_(NT, VPT, KA, W) SolveVariant{NT, VPT, KA, W, rkab_kernel<NT, VPT, ELT_F32, KA, W>}
+#define V_(NT, VPT, KA, W) SolveVariant{NT, VPT, KA, W, rkab_kernel<NT, VPT, ELT_F32, KA, W>, 1, false}
+#define VJ_(NT, VPT, KA) SolveVariant{NT, VPT, KA, 1, rkab_kernel<NT, VPT, ELT_F32, KA, 1, 1, true>, 1, true}
+#define V2_(NT, VPT) SolveVariant{NT, VPT, false, 1, rkab_kernel<NT, VPT, ELT_F32, false, 1, 2>, 2, false}
 static const SolveVariant kF32[] = {
     V_(32, 1, true, 1),    V_(32, 2, true, 1),    V_(32, 4, true, 1),
     V_(128, 2, true, 1),   V_(128, 3, true, 1),   V_(128, 5, true, 1),
@@ -16,8 +18,16 @@ static const SolveVariant kF32[] = {
     V_(128, 2, false, 4),  V_(128, 3, false, 4),  V_(128, 5, false, 4),
     V_(256, 3, false, 4),  V_(256, 4, false, 4),  V_(256, 5, false, 4),  V_(256, 6, false, 4),
     V_(256, 8, false, 4),
+    V2_(128, 2), V2_(128, 5), V2_(256, 5), V2_(256, 8), V2_(256, 10),
+    VJ_(32, 1, true),   VJ_(32, 2, true),   VJ_(32, 4, true),
+    VJ_(128, 2, true),  VJ_(128, 3, true),  VJ_(128, 5, true),
+    VJ_(256, 3, true),  VJ_(256, 4, true),  VJ_(256, 5, true),  VJ_(256, 6, true),
+    VJ_(256, 8, true),  VJ_(256, 10, true),
+    VJ_(512, 6, false), VJ_(512, 8, false), VJ_(512, 10, false),
 };
 #undef V_
+#undef V2_
+#undef VJ_
 
 const SolveVariant* solve_variants_f32(int* count) {
     *count = (int)(sizeof(kF32) / sizeof(kF32[0]));

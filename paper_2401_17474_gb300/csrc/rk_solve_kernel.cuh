@@ -66,6 +66,10 @@ struct KParams {
     float* V;               // q x ldv
     int64_t ldv;
     float* chkpart;         // gridDim.x float4: per-CTA check partials of its x slice
+    int vrows;              // rows of V holding displacements (averaged, divided by q)
+    int jacobi;             // RKA with q workers spread over the CTAs (alpha = 1): CTA g
+                            // holds workers [g q / G, (g+1) q / G), each one projection per
+                            // round from the round's x; their sum is the CTA's row of V
     int q;
     int64_t alpha;
     int64_t rounds;
@@ -85,6 +89,18 @@ struct KParams {
     uint32_t row_bytes;     // bytes moved per row (multiple of 16)
     uint32_t stage_stride;  // bytes between stages in shared memory
 };
+
+// Projections a CTA makes per round: alpha, or with JAC its share of the q workers
+// (CTA g holds workers [g q / G, (g+1) q / G)).
+template <bool JAC>
+__device__ __forceinline__ int cta_projections(const KParams& p) {
+    if constexpr (!JAC) {
+        return (int)p.alpha;
+    } else {
+        const int G = (int)gridDim.x;
+        return (int)(((blockIdx.x + 1) * p.q) / G - (blockIdx.x * p.q) / G);
+    }
+}
 
 struct Ctrl {
     long long stop_t;   // producer issues projections t < stop_t
@@ -163,14 +179,16 @@ __device__ __forceinline__ float4 slice(const uint8_t* stg, int idx, int k, int 
 
 // Four stored elements of slice idx of a stage, widened to float32 (the FP8 row
 // scale is not applied here).
-template <int ELT>
+template <int ELT, bool JAC>
 __device__ void producer_loop(const KParams& p, uint8_t* stages, uint64_t* full, uint64_t* empty,
                               float4* meta, volatile Ctrl* ctrl, float4* pbuf) {
     const int lane = threadIdx.x & 31;
     const int S = p.stages;
-    const int64_t total = p.rounds * p.alpha;
+    const int per = cta_projections<JAC>(p);
+    const int64_t total = p.rounds * (int64_t)per;
     const uint32_t worker = p.same_stream ? 0u : (uint32_t)blockIdx.x;
     const uint64_t tbase = (uint64_t)p.round0 * (uint64_t)p.alpha;
+    const uint32_t w0 = JAC ? (uint32_t)((blockIdx.x * p.q) / (int)gridDim.x) : 0u;
     const uint64_t pol = policy_evict_first();
     int* status = &p.info->status;
     int64_t issued = 0;
@@ -181,8 +199,15 @@ __device__ void producer_loop(const KParams& p, uint8_t* stages, uint64_t* full,
         // the warp draws 32 rows at once (their indices do not depend on v) ...
         const int64_t tl = base + lane;
         if (tl < total) {
-            const uint32_t row = sample_row(p.seed, worker, p.stream_id, tbase + (uint64_t)tl, p.m,
-                                            p.thr64, p.alias);
+            // worker gamma's t-th draw; with jacobi, draw j of round r belongs to
+            // worker w0 + j and is its round0 + r-th projection
+            uint32_t wk = worker;
+            uint64_t tt = tbase + (uint64_t)tl;
+            if constexpr (JAC) {
+                wk = p.same_stream ? 0u : w0 + (uint32_t)(tl % per);
+                tt = (uint64_t)p.round0 + (uint64_t)(tl / per);
+            }
+            const uint32_t row = sample_row(p.seed, wk, p.stream_id, tt, p.m, p.thr64, p.alias);
             const float sc = (ELT == ELT_FP8) ? __ldg(p.row_scale + row) : 1.f;
             pbuf[lane] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row), sc);
         }
@@ -325,20 +350,20 @@ __device__ __forceinline__ void average_slice(const KParams& p, float4* avg, boo
     if (nc >= NT) {
         for (int c = c0 + tid; c < c1; c += NT) {
             const float4 xo = load_x_old(p, c, first);
-            const float4 acc = sum_column<kAvgBatch>(p, c, 0, p.q);
+            const float4 acc = sum_column<kAvgBatch>(p, c, 0, p.vrows);
             store_x(p, c, make_float4(fmaf(acc.x, rq, xo.x), fmaf(acc.y, rq, xo.y), fmaf(acc.z, rq, xo.z),
                                       fmaf(acc.w, rq, xo.w)), chk);
         }
         return;
     }
     int groups = NT / nc;
-    if (groups > p.q) groups = p.q;
-    const int per = (p.q + groups - 1) / groups;
+    if (groups > p.vrows) groups = p.vrows;
+    const int per = (p.vrows + groups - 1) / groups;
     const int cl = tid % nc, g = tid / nc;
     float4 xo = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid < nc) xo = load_x_old(p, c0 + tid, first);
     if (g < groups) {
-        const int ga = g * per, gb = min(p.q, ga + per);
+        const int ga = g * per, gb = min(p.vrows, ga + per);
         avg[g * nc + cl] = sum_column<kAvgBatch>(p, c0 + cl, ga, gb);
     }
     named_bar_sync(1, NT);
@@ -453,8 +478,13 @@ struct GroupIdx {
     __device__ static constexpr int gram(int r, int l) { return W + r * (r - 1) / 2 + l; }
 };
 
-template <int NT, int VPT, int ELT, bool KEEP_A, int W>
-__global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
+// MINB = CTAs per SM the variant is built for (its register budget): 2 lets the
+// grid hold two workers per SM (more workers per round, smaller per-CTA share).
+// JAC = the CTA sums independent single projections from the round's x (RKA with
+// the workers spread over the CTAs, KParams::jacobi); W = 1 only.
+template <int NT, int VPT, int ELT, bool KEEP_A, int W, int MINB = 1, bool JAC = false>
+__global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
+    static_assert(!JAC || W == 1, "independent projections are not grouped");
     static_assert(W == 1 || !KEEP_A, "look-ahead groups re-read their rows");
     static_assert(GroupIdx<W>::NV <= kRedSlots, "too many partial sums per group");
     extern __shared__ __align__(128) uint8_t smem[];
@@ -472,7 +502,9 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int64_t total = p.rounds * p.alpha;
+    const int64_t alpha_c = cta_projections<JAC>(p);   // projections per round in this CTA
+    const int64_t total = p.rounds * alpha_c;
+    constexpr bool jac = JAC;                     // dots from the round's x only
     int* status = &p.info->status;
 
     {
@@ -497,7 +529,7 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
         return;
     }
     if (warp == NW) {
-        producer_loop<ELT>(p, stages, full, empty, meta, ctrl, pbuf);
+        producer_loop<ELT, JAC>(p, stages, full, empty, meta, ctrl, pbuf);
         return;
     }
 
@@ -533,8 +565,8 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
     for (int64_t r = 0; r < p.rounds && ok; ++r) {
       if constexpr (W > 1) {
         constexpr int NV = GroupIdx<W>::NV;
-        for (int64_t j = 0; j < p.alpha; j += W) {
-            const int wc = (p.alpha - j) < W ? (int)(p.alpha - j) : W;
+        for (int64_t j = 0; j < alpha_c; j += W) {
+            const int wc = (alpha_c - j) < W ? (int)(alpha_c - j) : W;
             int sg[W];
             uint32_t pg[W];
             bool got = true;
@@ -647,7 +679,7 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
         float cprev = 0.f;
 #pragma unroll
         for (int k = 0; k < VPT; ++k) a[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int64_t j = 0; j < p.alpha; ++j, ++t) {
+        for (int64_t j = 0; j < alpha_c; ++j, ++t) {
             const bool got = wait_parity(&full[s], ph, p.timeout_ns, status);
             const uint8_t* stg = stages + (size_t)s * p.stage_stride;
             const float4 mb = meta[s];   // b_i, 1/||A_i||^2, row scale
@@ -665,8 +697,10 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
                 const float2 alo = make_float2(ak.x, ak.y), ahi = make_float2(ak.z, ak.w); \
                 p01 = __ffma2_rn(alo, make_float2(v[k].x, v[k].y), p01);                \
                 p23 = __ffma2_rn(ahi, make_float2(v[k].z, v[k].w), p23);                \
-                p01 = __ffma2_rn(alo, dlo, p01);                                        \
-                p23 = __ffma2_rn(ahi, dhi, p23);                                        \
+                if (!jac) {                                                             \
+                    p01 = __ffma2_rn(alo, dlo, p01);                                    \
+                    p23 = __ffma2_rn(ahi, dhi, p23);                                    \
+                }                                                                       \
                 d[k] = make_float4(dlo.x, dlo.y, dhi.x, dhi.y);                         \
                 a[k] = ak;                                                              \
             }
@@ -710,7 +744,7 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
             }
         }
       } else {
-        for (int64_t j = 0; j < p.alpha; ++j, ++t) {
+        for (int64_t j = 0; j < alpha_c; ++j, ++t) {
             const bool got = wait_parity(&full[s], ph, p.timeout_ns, status);
             const uint8_t* stg = stages + (size_t)s * p.stage_stride;
             const float4 mb = meta[s];   // b_i, 1/||A_i||^2, row scale
@@ -727,10 +761,12 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_kernel(const KParams p) {
                 p1 = fmaf(ak.y, v[k].y, p1);
                 p2 = fmaf(ak.z, v[k].z, p2);
                 p3 = fmaf(ak.w, v[k].w, p3);
-                p0 = fmaf(ak.x, d[k].x, p0);
-                p1 = fmaf(ak.y, d[k].y, p1);
-                p2 = fmaf(ak.z, d[k].z, p2);
-                p3 = fmaf(ak.w, d[k].w, p3);
+                if (!jac) {
+                    p0 = fmaf(ak.x, d[k].x, p0);
+                    p1 = fmaf(ak.y, d[k].y, p1);
+                    p2 = fmaf(ak.z, d[k].z, p2);
+                    p3 = fmaf(ak.w, d[k].w, p3);
+                }
             }
             if constexpr (KEEP_A) {
                 __syncwarp();
@@ -843,6 +879,8 @@ struct SolveVariant {
     bool keep_a;
     int w;              // rows per look-ahead group
     SolveKernelFn fn;
+    int minb;           // CTAs per SM the register budget allows (1 or 2)
+    bool jac;           // independent projections from the round's x (RKA spread over CTAs)
 };
 
 // Instantiation tables (one translation unit per stored type).

@@ -91,22 +91,31 @@ __global__ void scale_kernel(const double* __restrict__ w, int64_t n, const doub
     }
 }
 
-// Per-block partial sums of a_ij^2 (one warp per row, FP64; FP32 squares are exact in FP64).
+// Per-block partial sums of a_ij^2: one warp per row, each lane accumulating the
+// exact squares (a a = p + e, e = fma(a, a, -p)) in a compensated float32 pair
+// (TwoSum; about 2^-46 relative), the pairs combined in FP64 per block.  The
+// FP64 pipe of the device is slow, so no FP64 operation runs per element.
 __global__ void __launch_bounds__(kSpThreads) fro_rows_kernel(const float* __restrict__ A, int64_t m,
                                                               int64_t n, int64_t lda,
                                                               double* __restrict__ part) {
     __shared__ double sh[kSpThreads];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * (kSpThreads / 32) + warp; i < m;
          i += (int64_t)gridDim.x * (kSpThreads / 32)) {
         const float* a = A + i * lda;
         for (int64_t j = lane; j < n; j += 32) {
-            const double t = (double)__ldg(a + j);
-            acc = fma(t, t, acc);
+            const float t = __ldcs(a + j);
+            const float p = __fmul_rn(t, t);
+            const float e = fmaf(t, t, -p);
+            const float s = __fadd_rn(hi, p);
+            const float bb = __fsub_rn(s, hi);
+            const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+            hi = s;
+            lo = __fadd_rn(lo, __fadd_rn(err, e));
         }
     }
-    const double s = block_sum(acc, sh);
+    const double s = block_sum((double)hi + (double)lo, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 

@@ -218,7 +218,7 @@ def test_argument_errors(rk, c1):
     with pytest.raises(rk.RkError):
         rk.rkab_solve(plan, b, q=2, alpha=1, rounds=1, omega=4.0)   # omega < 2q
     with pytest.raises(rk.RkError) as e:
-        rk.rkab_solve(plan, b, q=100000, alpha=1, rounds=1)
+        rk.rkab_solve(plan, b, q=100000, alpha=2, rounds=1)
     assert e.value.code == -3   # not co-resident: refused before launch
 
 
@@ -271,3 +271,43 @@ def test_wait_limit_ends_the_solve_with_a_status(rk):
     x, info = rk.rkab_solve(plan, b_t, q=4, alpha=500, rounds=3, seed=1, check_every=0)
     assert info.status == 0
     assert torch.isfinite(x).all()
+
+
+@pytest.mark.parametrize("alpha,rounds", [(1, 20), (25, 4)])
+def test_more_workers_than_sms_matches_oracle(rk, alpha, rounds):
+    """q above the SM count: RKA (alpha = 1) spreads the workers over one CTA per SM,
+    RKAB runs two workers per SM (the two-per-SM variants); same draws, x within 1e-4
+    of the oracle; RKAB beyond two workers per SM is refused."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    q = sms + 8
+    s = rk_inputs.gaussian_system(2000, 100, seed=0)
+    tab = oracle.table(s.A)
+    plan = rk.rk_setup(_padded(s.A, rk))
+    x, info = rk.rkab_solve(plan, _dev(s.b), q=q, alpha=alpha, rounds=rounds, seed=3,
+                            check_every=0)
+    assert info.status == 0 and info.rounds_done == rounds
+    x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=q, alpha=alpha,
+                      rounds=rounds, seed=3, tab=tab)
+    assert _rel(x.cpu().numpy(), x_o) < TOL
+    with pytest.raises(rk.RkError) as e:
+        rk.rkab_solve(plan, _dev(s.b), q=2 * sms + 1, alpha=2, rounds=1)
+    assert e.value.code == -3
+
+
+@pytest.mark.parametrize("mult,extra,omega", [(4, 3, 1.0), (16, 0, None), (7, 11, None)])
+def test_rka_many_workers_matches_oracle(rk, mult, extra, omega):
+    """RKA with q = mult * SMs + extra workers (uneven shares per CTA), unit weight or the
+    optimal weight of Eq. (best_alpha): x within 1e-4 of the oracle after 15 rounds."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    q = mult * sms + extra
+    s = rk_inputs.gaussian_system(4000, 200, seed=1)
+    tab = oracle.table(s.A)
+    if omega is None:
+        lmin, lmax, fro2 = oracle.spectrum(s.A)
+        omega = float(np.float32(oracle.alpha_star(q, lmin / fro2, lmax / fro2)))
+    plan = rk.rk_setup(_padded(s.A, rk))
+    x, info = rk.rka_solve(plan, _dev(s.b), q=q, rounds=15, seed=9, omega=omega, check_every=0)
+    assert info.status == 0 and info.rounds_done == 15
+    x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(200), q=q, alpha=1, rounds=15,
+                      seed=9, tab=tab, omega=omega)
+    assert _rel(x.cpu().numpy(), x_o) < TOL
