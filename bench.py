@@ -287,7 +287,7 @@ def extra_cells(rk, A, plan, b, xs, n, tol, max_rounds):
     import torch
     x0 = torch.zeros(n, dtype=torch.float32, device=b.device)
     x = torch.empty_like(x0)
-    sp = rk.spectrum(A, k=8)
+    sp = rk.spectrum(A, k=4)
     out = {}
     cells = []
     for q in (132, 32, 8):
@@ -356,9 +356,9 @@ def extra_relaxed(rk, A, plan, b, xs, n, tol):
     x = torch.empty_like(x0)
     out = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    rk.spectrum(A, k=8)   # warm-up
+    rk.spectrum(A, k=4)   # warm-up
     e0.record()
-    sp = rk.spectrum(A, k=8)
+    sp = rk.spectrum(A, k=4)
     e1.record()
     torch.cuda.synchronize()
     out["spectrum"] = {"ms": round(e0.elapsed_time(e1), 2), "lanczos_steps": sp.steps,
@@ -527,7 +527,7 @@ def run_precision(args, rk, dev):
     units = q * alpha * inf.rounds_done * args.steps
     out = {"fp32_plain": {"ms": round(total / args.steps, 2), "rounds": inf.rounds_done,
                           "metric": inf.last_metric}}
-    sp = rk.spectrum(A, k=8)
+    sp = rk.spectrum(A, k=4)
     for kind in ("bf16", "fp8"):
         try:
             Aq, sc = rk.quantize(A, kind)
@@ -610,7 +610,7 @@ def run_ours(args):
     elem = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
     solver = rk.Solver(plan0, q)
     if args.omega == "star":
-        omega, _ = rk.optimal_weight(A, q, k=8)
+        omega, _ = rk.optimal_weight(A, q, k=4)
     else:
         omega = float(args.omega)
     opts = rk.make_opts(check_every=1, tol=args.tol, x_ref=xs, cluster_size=args.cluster,
