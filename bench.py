@@ -68,11 +68,13 @@ def parse():
     ap.add_argument("--omega", default="1",
                     help="relaxation of the timed solve: a number, or 'star' for alpha* of "
                          "Eq. (best_alpha) from the GPU spectrum estimate (computed before timing)")
-    ap.add_argument("--workload", default="consistent", choices=["consistent", "lsq", "precision"],
+    ap.add_argument("--workload", default="consistent",
+                    choices=["consistent", "lsq", "precision", "horizon"],
                     help="consistent: 80000 x 10000 to 1e-6 (default); lsq: 200000 x 20000 "
                          "row-scaled inconsistent system, budget of rounds with the normal-equation "
                          "criterion logged every round; precision: 1e6 x 16000, FP32 vs BF16/FP8 "
-                         "+ refinement to 1e-6")
+                         "+ refinement to 1e-6; horizon: 80000 x 1000 inconsistent system, error "
+                         "to x_LS and residual along RKA / RKAB runs for several worker counts")
     return ap.parse_args()
 
 
@@ -566,6 +568,62 @@ def run_precision(args, rk, dev):
     return line
 
 
+def run_horizon(args, rk, dev):
+    """Section 3.5: on an inconsistent 80000 x 1000 system (b = A x* + N(0, 1)), RK, RKA and
+    RKAB stop at a convergence horizon around x_LS that shrinks with the worker count q.
+    The error ||x - x_LS|| and the residual ||A x - b|| are logged every `step` rounds:
+    RKA (alpha = 1) with the unit weight and with alpha*, 30000 rounds, step 100; RKAB with
+    alpha = n, 30 rounds, step 1; q in {1, 2, 20, 50}.  x_LS is a reference solution of the
+    measurement (LAPACK-style QR in FP64 through torch), not part of the solver."""
+    import torch
+
+    import rk_inputs
+    m, n = 80000, 1000
+    A, b, _ = rk_inputs.gaussian_system_torch(m, n, seed=args.seed, noise=1.0, device=str(dev))
+    x_ls = torch.linalg.lstsq(A.double(), b.double().unsqueeze(1)).solution.squeeze(1)
+    r_ls = float(torch.linalg.norm(A.double() @ x_ls - b.double()))
+    plan = rk.rk_setup(A)
+    sp = rk.spectrum(A, k=8)
+    res = rk.Residual(m, n, dev)
+    norms = torch.zeros(2, dtype=torch.float64, device=dev)
+    out = {"x_ls_norm": float(torch.linalg.norm(x_ls)), "residual_ls": r_ls, "runs": {}}
+    t_total = 0.0
+    for method, alpha, rounds, step in (("rka", 1, 30000, 100), ("rkab", n, 30, 1)):
+        for q in (1, 2, 20, 50):
+            weights = [("omega1", 1.0)]
+            if method == "rka" and q > 1:
+                weights.append(("alpha_star", rk.alpha_star(q, sp.s_min, sp.s_max)))
+            for wname, omega in weights:
+                solver = rk.Solver(plan, q)
+                xa = torch.zeros(n, dtype=torch.float32, device=dev)
+                xb = torch.empty_like(xa)
+                err, resid = [], []
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for r0 in range(0, rounds, step):
+                    o = rk.make_opts(check_every=0, round0=r0, omega=omega)
+                    solver.launch(b, xa, xb, alpha, step, args.seed, o)
+                    res.launch(A, b, xb, None, norms, False)
+                    err.append(float(torch.linalg.norm(xb.double() - x_ls)))
+                    resid.append(float(norms[0]))
+                    xa, xb = xb, xa
+                e1.record()
+                torch.cuda.synchronize(dev)
+                t_total += e0.elapsed_time(e1)
+                tail = err[len(err) * 3 // 4:]
+                out["runs"][f"{method}_q{q}_{wname}"] = {
+                    "omega": omega, "rounds": rounds, "step": step,
+                    "error": [round(e, 6) for e in err[:: max(1, len(err) // 30)]],
+                    "residual": [round(v, 4) for v in resid[:: max(1, len(resid) // 30)]],
+                    "horizon_error": sum(tail) / len(tail),
+                    "final_residual_over_ls": resid[-1] / r_ls}
+    line = _base_line(args, METRIC, 0.0, UNIT, t_total, {
+        "workload": f"horizon_inconsistent_{m}x{n}_noise1", "m": m, "n": n,
+        "note": "value unused: this workload logs error and residual curves"}, None, None)
+    line["horizon"] = out
+    return line
+
+
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
@@ -587,7 +645,7 @@ def run_ours(args):
 
     if args.workload != "consistent":
         if rank == 0:
-            fn = run_lsq if args.workload == "lsq" else run_precision
+            fn = {"lsq": run_lsq, "precision": run_precision, "horizon": run_horizon}[args.workload]
             print(json.dumps(fn(args, rk, dev)), flush=True)
         if ws > 1:
             import torch.distributed as dist
