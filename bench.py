@@ -392,6 +392,32 @@ def extra_relaxed(rk, A, plan, b, xs, n, tol):
     return out
 
 
+def extra_sampling(rk, A, plan, b, xs, n, tol):
+    """Full-matrix sampling against the Distributed Approach's row blocks (Section 3.3.1,
+    Table 1): rounds and time to tolerance of RKA with alpha* (q = 2 .. 16, and 4864) and of
+    RKAB with alpha = n (q = 132), same system."""
+    import torch
+    x0 = torch.zeros(n, dtype=torch.float32, device=b.device)
+    x = torch.empty_like(x0)
+    sp = rk.spectrum(A, k=4)
+    out = {}
+    cells = [(f"rka_q{q}_alpha_star", q, 1, rk.alpha_star(q, sp.s_min, sp.s_max), 400000)
+             for q in (2, 4, 8, 16, 4864)]
+    cells.append(("rkab_q132_alpha_n", 132, n, 1.0, 400))
+    for name, q, alpha, omega, rounds in cells:
+        for mode in ("full", "blocks"):
+            try:
+                s = rk.Solver(plan, q)
+                o = rk.make_opts(check_every=1, tol=tol, x_ref=xs, omega=omega, sampling=mode)
+                t = _timed(lambda: s.launch(b, x0, x, alpha, rounds, 0, o), reps=1)
+                inf = s.info()
+                out[f"{name}_{mode}"] = {"ms": round(t, 2), "rounds": inf.rounds_done,
+                                         "metric": inf.last_metric, "status": inf.status}
+            except Exception as e:
+                out[f"{name}_{mode}"] = {"error": str(e)}
+    return out
+
+
 def extra_adjoint(rk, dev, seed):
     """Backward pass of the differentiation workload 50000 x 5000 (b = A x* + N(0, 1e-3^2),
     L = 0.5 ||x - x_t||^2): A^T copy and plan, minimum-norm solve on A^T (16-CTA clusters),
@@ -796,6 +822,7 @@ def run_ours(args):
                         ("precision", lambda: extra_precision(rk, A, plan0, b, xs, n, q, alpha,
                                                               args.tol)),
                         ("relaxed", lambda: extra_relaxed(rk, A, plan0, b, xs, n, args.tol)),
+                        ("sampling", lambda: extra_sampling(rk, A, plan0, b, xs, n, args.tol)),
                         ("adjoint", lambda: extra_adjoint(rk, dev, args.seed))):
             try:
                 extras[key] = fn()
@@ -833,6 +860,7 @@ def run_ours(args):
             line["precision"] = extras.get("precision")
             line["adjoint"] = extras.get("adjoint")
             line["relaxed"] = extras.get("relaxed")
+            line["sampling"] = extras.get("sampling")
             best = (extras.get("relaxed") or {}).get("best")
             if best:
                 line["time_to_tol_best"] = best

@@ -83,7 +83,22 @@ typedef struct {
                               per group and the projections resolved by a scalar
                               recurrence (same result as one row at a time in exact
                               arithmetic); 0 = chosen by the library               [0]   */
+    int sampling;          /* row selection (rk_sampling):
+                              RK_SAMPLE_FULL   every worker draws from the whole law of
+                                               Eq. (prob_line) (alias table)
+                              RK_SAMPLE_BLOCKS the Distributed Approach of Section 3.3.1:
+                                               worker g of q draws only from its block of
+                                               rows [g m / q, (g+1) m / q), with probability
+                                               ||A_i||^2 / (the block's sum)
+                              RK_SAMPLE_CYCLIC worker g sweeps the rows in order from
+                                               g m / q: row (g m / q + t) mod m (Section 2.1,
+                                               the cyclic Kaczmarz method for q = 1)   [FULL] */
+    const float *row_weight;  /* device, m floats or NULL: per-row weights w_i of Eq.
+                              (rka_eq), multiplying omega in each projection        [NULL]*/
 } rk_opts;
+
+/* Row selection of rk_opts.sampling. */
+typedef enum { RK_SAMPLE_FULL = 0, RK_SAMPLE_BLOCKS = 1, RK_SAMPLE_CYCLIC = 2 } rk_sampling;
 
 void rk_opts_default(rk_opts *opts);
 
@@ -142,6 +157,16 @@ void rk_plan_destroy(rk_plan *plan);
 /* Test hook: out[k] = draw of (seed, worker, t0 + k, stream_id), k < count (device, uint32). */
 int rk_sample_indices(const rk_plan *plan, uint64_t seed, uint32_t worker, uint32_t stream_id,
                       uint64_t t0, int64_t count, uint32_t *out, void *stream);
+
+/* Test hook for every row selection: out[k] = row of worker `worker` of q at projection
+ * t0 + k under `sampling` (rk_sampling).  RK_SAMPLE_BLOCKS draws with the same Philox
+ * words: c = floor(u T_g / 2^64) with T_g the integer weight of the worker's block, and the
+ * row is the one whose prefix interval [P_i, P_i + K_i) of the plan holds P_start + c (a
+ * block of zero weight gives row m, and a solve with it fails with RK_EINVAL).
+ * RK_SAMPLE_CYCLIC uses no random bits. */
+int rk_sample_indices_ex(const rk_plan *plan, uint64_t seed, uint32_t worker, uint32_t q,
+                         uint32_t stream_id, int sampling, uint64_t t0, int64_t count,
+                         uint32_t *out, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Solve: RKAB, Section 3.4.1 and Algorithm 3.  Each of q workers starts a   */

@@ -76,6 +76,15 @@ def lib():
                                ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                _u64p, _u32p, ctypes.c_int, ctypes.c_int, _f64p, ctypes.c_double,
                                _i64p, _f64p]
+        L.orc_rkab_ext.argtypes = L.orc_rkab.argtypes + [ctypes.c_int, _u64p, _f64p]
+        L.orc_select_row.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                     ctypes.c_int, ctypes.c_uint32, ctypes.c_int64, _u64p, _u32p,
+                                     _u64p]
+        L.orc_select_row.restype = ctypes.c_int64
+        L.orc_select_rows.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                      ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
+                                      ctypes.c_int64, _u64p, _u32p, _u64p, _i64p]
+        L.orc_select_rows.restype = None
         L.orc_rkab_round_workers.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int64,
                                              ctypes.c_int64, _f64p, _f64p, _f64p, ctypes.c_int,
                                              ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
@@ -163,10 +172,23 @@ def table(A) -> Table:
     return Table(K, T, L, thr, al)
 
 
-def sample_rows(tab: Table, seed: int, worker: int, t0: int, count: int, stream: int = 0):
+SAMPLING = {"full": 0, "blocks": 1, "cyclic": 2}
+
+
+def sample_rows(tab: Table, seed: int, worker: int, t0: int, count: int, stream: int = 0,
+                sampling="full", q: int = 1):
+    """Row choices t0 .. t0+count-1 of worker `worker` of q under a row selection
+    ('full': the law of Eq. (prob_line); 'blocks': the worker's row block; 'cyclic')."""
     out = np.zeros(count, np.int64)
-    lib().orc_sample_rows(seed, worker, stream, t0, count, tab.m, _p(tab.thr64, _u64p),
-                          _p(tab.alias, _u32p), _p(out, _i64p))
+    mode = SAMPLING[sampling] if isinstance(sampling, str) else int(sampling)
+    if mode == 0 and q == 1:
+        lib().orc_sample_rows(seed, worker, stream, t0, count, tab.m, _p(tab.thr64, _u64p),
+                              _p(tab.alias, _u32p), _p(out, _i64p))
+    else:
+        K = np.ascontiguousarray(tab.K, np.uint64)
+        lib().orc_select_rows(mode, seed, worker, q, stream, t0, count, tab.m,
+                              _p(tab.thr64, _u64p), _p(tab.alias, _u32p), _p(K, _u64p),
+                              _p(out, _i64p))
     return out
 
 
@@ -210,8 +232,10 @@ def rka_formula(A, b, x0, q, iters, seed, tab: Table, stream=0, omega=1.0):
 
 
 def rkab(A, b, x0, q, alpha, rounds, seed, tab: Table, round0=0, stream=0, omega=1.0,
-         same_stream=False, threads=1, x_ref=None, tol=0.0, want_trace=False):
-    """RKAB rounds; returns x (and rounds done, trace of rel. errors if x_ref given)."""
+         same_stream=False, threads=1, x_ref=None, tol=0.0, want_trace=False, sampling="full",
+         row_weight=None):
+    """RKAB rounds; returns x (and rounds done, trace of rel. errors if x_ref given).
+    sampling: row selection ('full', 'blocks', 'cyclic'); row_weight: w_i of Eq. (rka_eq)."""
     A, m, n, lda = _mat(A)
     b = _vec64(b, m)
     x0 = _vec64(x0, n)
@@ -219,11 +243,15 @@ def rkab(A, b, x0, q, alpha, rounds, seed, tab: Table, round0=0, stream=0, omega
     done = ctypes.c_int64(0)
     xr = None if x_ref is None else _vec64(x_ref, n)
     trace = np.full(max(rounds, 1), np.nan) if (want_trace and xr is not None) else None
-    _check(lib().orc_rkab(_p(A, _f32p), m, n, lda, _p(b, _f64p), _p(x0, _f64p), _p(x, _f64p),
-                          q, alpha, rounds, round0, seed, stream, omega, _p(tab.thr64, _u64p),
-                          _p(tab.alias, _u32p), int(bool(same_stream)), threads,
-                          None if xr is None else _p(xr, _f64p), tol, ctypes.byref(done),
-                          None if trace is None else _p(trace, _f64p)), "rkab")
+    mode = SAMPLING[sampling] if isinstance(sampling, str) else int(sampling)
+    K = np.ascontiguousarray(tab.K, np.uint64)
+    wv = None if row_weight is None else _vec64(row_weight, m)
+    _check(lib().orc_rkab_ext(_p(A, _f32p), m, n, lda, _p(b, _f64p), _p(x0, _f64p), _p(x, _f64p),
+                              q, alpha, rounds, round0, seed, stream, omega, _p(tab.thr64, _u64p),
+                              _p(tab.alias, _u32p), int(bool(same_stream)), threads,
+                              None if xr is None else _p(xr, _f64p), tol, ctypes.byref(done),
+                              None if trace is None else _p(trace, _f64p), mode, _p(K, _u64p),
+                              None if wv is None else _p(wv, _f64p)), "rkab")
     if want_trace:
         return x, int(done.value), trace[: int(done.value)]
     if xr is not None:

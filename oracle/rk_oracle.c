@@ -18,10 +18,15 @@
  *   orc_row_weights     exact integer encoding of the sampling law, Eq. (prob_line)
  *   orc_alias_build     alias table of that law by the sweeping construction
  *   orc_sample_row      one draw from the law for (seed, worker, projection)
+ *   orc_select_row      row choice of a worker under the three selections: the
+ *                       law above, the row blocks of the Distributed Approach
+ *                       (Section 3.3.1), the cyclic sweep (Section 2.1)
  *   orc_rk              RK, Eq. (alg) with rows drawn by Eq. (prob_line)
  *   orc_rka_formula     RKA iteration written as Eq. (rka_uni_weights)
  *   orc_rkab            RKAB (Section 3.4.1, Algorithm 3): q workers, alpha
  *                       projections each, then the average
+ *   orc_rkab_ext        the same with a row selection and per-row weights w_i of
+ *                       Eq. (rka_eq)
  *   orc_residual        r = b - A x, ||r||, ||A^T r||
  *   orc_bf16_rne        FP32 -> BF16 round-to-nearest-even
  *   orc_fp8e4m3_rne     FP32 -> FP8 e4m3 (OCP "fn" variant) round-to-nearest-even,
@@ -226,6 +231,49 @@ int64_t orc_sample_row(uint64_t seed, uint64_t t, uint32_t worker, uint32_t stre
     return u2 < thr64[c] ? c : (int64_t)alias[c];
 }
 
+/* Row of worker g of q at projection counter t under a row selection:
+ *   0  the whole law (orc_sample_row);
+ *   1  the Distributed Approach (Section 3.3.1): worker g keeps to its block of
+ *      rows [g m / q, (g+1) m / q) and draws row i of it with probability
+ *      K_i / T_g, T_g = the block's sum of K.  The Philox words are those of
+ *      orc_sample_row; c = floor(u T_g / 2^64) and the row is the one whose
+ *      interval [S_i, S_i + K_i) holds S_start + c, with S the exclusive prefix
+ *      sum of K (found by a plain scan).  Returns -1 for a block of weight 0;
+ *   2  the cyclic sweep (Section 2.1): row (g m / q + t) mod m.                */
+int64_t orc_select_row(int sampling, uint64_t seed, uint64_t t, uint32_t g, int q, uint32_t stream,
+                       int64_t m, const uint64_t *thr64, const uint32_t *alias, const uint64_t *K)
+{
+    if (sampling == 0) return orc_sample_row(seed, t, g, stream, m, thr64, alias);
+    int64_t start = (int64_t)(((u128)g * (u128)m) / (u128)q);
+    int64_t end = (int64_t)(((u128)(g + 1) * (u128)m) / (u128)q);
+    if (sampling == 2) return (int64_t)(((uint64_t)start + t) % (uint64_t)m);
+    uint64_t tg = 0;
+    for (int64_t i = start; i < end; ++i) tg += K[i];
+    if (tg == 0) return -1;
+    uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), g, stream};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    uint64_t u = (uint64_t)r[0] | ((uint64_t)r[1] << 32);
+    uint64_t c = (uint64_t)(((u128)u * (u128)tg) >> 64);
+    /* walk the block: the row whose share [acc, acc + K_i) of the block holds c */
+    uint64_t acc = 0;
+    for (int64_t i = start; i < end; ++i) {
+        if (c < acc + K[i]) return i;
+        acc += K[i];
+    }
+    return -1;
+}
+
+/* count consecutive row choices of worker g of q: out[k] = row at t = t0 + k. */
+void orc_select_rows(int sampling, uint64_t seed, uint32_t g, int q, uint32_t stream, uint64_t t0,
+                     int64_t count, int64_t m, const uint64_t *thr64, const uint32_t *alias,
+                     const uint64_t *K, int64_t *out)
+{
+    for (int64_t k = 0; k < count; ++k)
+        out[k] = orc_select_row(sampling, seed, t0 + (uint64_t)k, g, q, stream, m, thr64, alias, K);
+}
+
 /* count consecutive draws of one worker: out[k] = draw at t = t0 + k. */
 void orc_sample_rows(uint64_t seed, uint32_t worker, uint32_t stream, uint64_t t0, int64_t count,
                      int64_t m, const uint64_t *thr64, const uint32_t *alias, int64_t *out)
@@ -340,13 +388,15 @@ int orc_rka_formula(const float *A, int64_t m, int64_t n, int64_t lda, const dou
 /* threads (the shared-memory structure of Algorithm 3); the result does not */
 /* depend on the thread count.                                              */
 /* ------------------------------------------------------------------------- */
-int orc_rkab(const float *A, int64_t m, int64_t n, int64_t lda, const double *b,
-             const double *x0, double *x, int q, int64_t alpha, int64_t rounds,
-             int64_t round0, uint64_t seed, uint32_t stream, double omega,
-             const uint64_t *thr64, const uint32_t *alias, int same_stream, int threads,
-             const double *x_ref, double tol, int64_t *rounds_done, double *trace)
+int orc_rkab_ext(const float *A, int64_t m, int64_t n, int64_t lda, const double *b,
+                 const double *x0, double *x, int q, int64_t alpha, int64_t rounds,
+                 int64_t round0, uint64_t seed, uint32_t stream, double omega,
+                 const uint64_t *thr64, const uint32_t *alias, int same_stream, int threads,
+                 const double *x_ref, double tol, int64_t *rounds_done, double *trace,
+                 int sampling, const uint64_t *K, const double *row_weight)
 {
     if (q < 1 || alpha < 1 || rounds < 0) return ORC_EINVAL;
+    if (sampling != 0 && (same_stream || (sampling == 1 && !K))) return ORC_EINVAL;
     double *w = (double *)malloc(sizeof(double) * (size_t)m);
     double *V = (double *)malloc(sizeof(double) * (size_t)q * (size_t)n);
     if (!w || !V) { free(w); free(V); return ORC_ENOMEM; }
@@ -365,8 +415,10 @@ int orc_rkab(const float *A, int64_t m, int64_t n, int64_t lda, const double *b,
             uint32_t worker = same_stream ? 0u : (uint32_t)g;
             for (int64_t j = 0; j < alpha; ++j) {
                 uint64_t t = (uint64_t)(round * alpha + j);
-                int64_t i = orc_sample_row(seed, t, worker, stream, m, thr64, alias);
-                project(A + i * lda, b[i], w[i], omega, v, n);
+                int64_t i = orc_select_row(sampling, seed, t, worker, q, stream, m, thr64, alias, K);
+                if (i < 0) continue;   /* a block of weight 0 (reported by the caller) */
+                double wi = row_weight ? row_weight[i] : 1.0;
+                project(A + i * lda, b[i], w[i], omega * wi, v, n);
             }
         }
         for (int64_t j = 0; j < n; ++j) {
@@ -384,6 +436,18 @@ int orc_rkab(const float *A, int64_t m, int64_t n, int64_t lda, const double *b,
     if (rounds_done) *rounds_done = done;
     free(w); free(V);
     return ORC_OK;
+}
+
+/* RKAB with the whole law and unit weights. */
+int orc_rkab(const float *A, int64_t m, int64_t n, int64_t lda, const double *b,
+             const double *x0, double *x, int q, int64_t alpha, int64_t rounds,
+             int64_t round0, uint64_t seed, uint32_t stream, double omega,
+             const uint64_t *thr64, const uint32_t *alias, int same_stream, int threads,
+             const double *x_ref, double tol, int64_t *rounds_done, double *trace)
+{
+    return orc_rkab_ext(A, m, n, lda, b, x0, x, q, alpha, rounds, round0, seed, stream, omega,
+                        thr64, alias, same_stream, threads, x_ref, tol, rounds_done, trace, 0,
+                        NULL, NULL);
 }
 
 /* Worker iterates of one RKAB round (before the average), for the Jensen

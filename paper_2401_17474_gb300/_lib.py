@@ -39,6 +39,8 @@ class RkOpts(ctypes.Structure):
         ("cluster_size", ctypes.c_int),
         ("timeout_s", ctypes.c_double),
         ("lookahead", ctypes.c_int),
+        ("sampling", ctypes.c_int),
+        ("row_weight", ctypes.c_void_p),
     ]
 
 
@@ -57,6 +59,9 @@ _SIG = {
     "rk_plan_destroy": (None, [_V]),
     "rk_sample_indices": (ctypes.c_int, [_V, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                          ctypes.c_uint64, ctypes.c_int64, _V, _V]),
+    "rk_sample_indices_ex": (ctypes.c_int, [_V, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                            ctypes.c_uint32, ctypes.c_int, ctypes.c_uint64,
+                                            ctypes.c_int64, _V, _V]),
     "rk_solve_workspace_bytes": (ctypes.c_size_t, [_V, ctypes.c_int]),
     "rkab_solve": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_uint64, ctypes.POINTER(RkOpts), _V, ctypes.c_size_t,

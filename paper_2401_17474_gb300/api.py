@@ -125,11 +125,18 @@ def rk_setup(A: torch.Tensor, dtype: str = "f32", row_scale=None, stream=None,
 
 
 def rk_sample_indices(plan: Plan, seed: int, worker: int, t0: int, count: int,
-                      stream_id: int = 0, stream=None) -> torch.Tensor:
-    """Row draws t0 .. t0+count-1 of one worker (uint32 values in an int32 tensor)."""
+                      stream_id: int = 0, stream=None, sampling="full", q: int = 1) -> torch.Tensor:
+    """Row draws t0 .. t0+count-1 of one worker (uint32 values in an int32 tensor); with
+    sampling 'blocks' or 'cyclic' the worker is one of q (rk_sample_indices_ex)."""
     out = torch.empty(max(count, 1), dtype=torch.int32, device=plan.device)
-    check(_lib.load().rk_sample_indices(plan.handle, seed, worker, stream_id, t0, count,
-                                        _ptr(out), _stream(stream)), "rk_sample_indices")
+    mode = SAMPLING[sampling] if isinstance(sampling, str) else int(sampling)
+    if mode == 0 and q == 1:
+        check(_lib.load().rk_sample_indices(plan.handle, seed, worker, stream_id, t0, count,
+                                            _ptr(out), _stream(stream)), "rk_sample_indices")
+    else:
+        check(_lib.load().rk_sample_indices_ex(plan.handle, seed, worker, q, stream_id, mode, t0,
+                                               count, _ptr(out), _stream(stream)),
+              "rk_sample_indices_ex")
     return out[:count]
 
 
@@ -140,8 +147,12 @@ class SolveInfo:
     last_metric: float
 
 
+SAMPLING = {"full": 0, "blocks": 1, "cyclic": 2}
+
+
 def make_opts(omega=1.0, check_every=1, tol=0.0, x_ref=None, round0=0, stream_id=0,
-              same_stream=False, cluster_size=0, timeout_s=10.0, lookahead=0) -> RkOpts:
+              same_stream=False, cluster_size=0, timeout_s=10.0, lookahead=0,
+              sampling="full", row_weight=None) -> RkOpts:
     o = RkOpts()
     _lib.load().rk_opts_default(ctypes.byref(o))
     o.omega = float(omega)
@@ -155,6 +166,8 @@ def make_opts(omega=1.0, check_every=1, tol=0.0, x_ref=None, round0=0, stream_id
     o.cluster_size = int(cluster_size)
     o.timeout_s = float(timeout_s)
     o.lookahead = int(lookahead)
+    o.sampling = SAMPLING[sampling] if isinstance(sampling, str) else int(sampling)
+    o.row_weight = None if row_weight is None else row_weight.data_ptr()
     return o
 
 
@@ -193,8 +206,11 @@ def _vec(t, n, name):
 def rkab_solve(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, rounds: int = 1,
                seed: int = 0, *, omega=1.0, x_ref=None, tol=0.0, check_every=1, round0=0,
                stream_id=0, same_stream=False, timeout_s=10.0, lookahead=0, cluster_size=0,
-               out=None, solver=None, stream=None, raise_on_error=True):
-    """RKAB solve (alpha projections per worker between averages); returns (x, info)."""
+               sampling="full", row_weight=None, out=None, solver=None, stream=None,
+               raise_on_error=True):
+    """RKAB solve (alpha projections per worker between averages); returns (x, info).
+    sampling: 'full' (Eq. (prob_line)), 'blocks' (per-worker row blocks), 'cyclic';
+    row_weight: optional per-row weights w_i (m floats on the device)."""
     b = _vec(b, plan.m, "b")
     if x0 is None:
         x0 = torch.zeros(plan.n, dtype=torch.float32, device=plan.device)
@@ -203,8 +219,10 @@ def rkab_solve(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, rounds: int =
     if x_ref is not None:
         x_ref = _vec(x_ref, plan.n, "x_ref")
     s = solver if solver is not None else Solver(plan, q)
+    if row_weight is not None:
+        row_weight = _vec(row_weight, plan.m, "row_weight")
     opts = make_opts(omega, check_every, tol, x_ref, round0, stream_id, same_stream, cluster_size,
-                     timeout_s, lookahead)
+                     timeout_s, lookahead, sampling, row_weight)
     s.launch(b, x0, x, alpha, rounds, seed, opts, stream)
     info = s.info(stream)
     if raise_on_error and info.status != _lib.RK_OK:

@@ -86,6 +86,14 @@ void rk_opts_default(rk_opts* o) {
     o->cluster_size = 0;
     o->timeout_s = 10.0;
     o->lookahead = 0;
+    o->sampling = RK_SAMPLE_FULL;
+    o->row_weight = nullptr;
+}
+
+// Row selection: a known mode; per-worker modes need the workers' own streams.
+static bool sampling_ok(const rk_opts& o) {
+    if (o.sampling == RK_SAMPLE_FULL) return true;
+    return (o.sampling == RK_SAMPLE_BLOCKS || o.sampling == RK_SAMPLE_CYCLIC) && !o.same_stream;
 }
 
 const char* rk_strerror(int code) {
@@ -177,6 +185,16 @@ int rk_sample_indices(const rk_plan* plan, uint64_t seed, uint32_t worker, uint3
                                  static_cast<cudaStream_t>(stream));
 }
 
+int rk_sample_indices_ex(const rk_plan* plan, uint64_t seed, uint32_t worker, uint32_t q,
+                         uint32_t stream_id, int sampling, uint64_t t0, int64_t count,
+                         uint32_t* out, void* stream) {
+    if (!plan || count < 0 || (count > 0 && !out) || q < 1 || worker >= q ||
+        (sampling != RK_SAMPLE_FULL && sampling != RK_SAMPLE_BLOCKS && sampling != RK_SAMPLE_CYCLIC))
+        return RK_EINVAL;
+    return launch_sample_indices_ex(&plan->p, seed, worker, q, stream_id, sampling, t0, count, out,
+                                    static_cast<cudaStream_t>(stream));
+}
+
 size_t rk_solve_workspace_bytes(const rk_plan* plan, int q) {
     if (!plan || q < 1) return 0;
     return solve_ws_bytes(&plan->p, q);
@@ -194,7 +212,8 @@ int rkab_solve(const rk_plan* plan, const float* b, const float* x0, float* x, i
         !(o.timeout_s > 0.0) || (o.criterion == 1 && !o.x_ref) || o.criterion < 0 ||
         o.criterion > 1 || !(o.lookahead == 0 || o.lookahead == 1 || o.lookahead == 2 ||
                              o.lookahead == 4 || o.lookahead == 6) ||
-        o.cluster_size < 0 || o.cluster_size > 16 || (o.cluster_size & (o.cluster_size - 1)) != 0)
+        o.cluster_size < 0 || o.cluster_size > 16 || (o.cluster_size & (o.cluster_size - 1)) != 0 ||
+        !sampling_ok(o))
         return RK_EINVAL;
     if (((uintptr_t)workspace & 255u) != 0) return RK_EALIGN;
     if (ws_bytes < solve_ws_bytes(&plan->p, q)) return RK_EWORKSPACE;
@@ -271,7 +290,7 @@ int rkab_refine(const rk_plan* lowp, const float* A32, int64_t lda32, const floa
     rk_opts_default(&o);
     if (opts) o = *opts;
     if (!omega_ok(o.omega, q) || !(o.timeout_s > 0.0) ||
-        (o.criterion == 1 && !o.x_ref) || o.criterion < 0 || o.criterion > 1)
+        (o.criterion == 1 && !o.x_ref) || o.criterion < 0 || o.criterion > 1 || !sampling_ok(o))
         return RK_EINVAL;
     if (ws_bytes < refine_ws_bytes(&lowp->p, q)) return RK_EWORKSPACE;
     return run_refine(&lowp->p, A32, lda32, b, x0, x, q, alpha, inner_rounds, max_outer, seed, o,
@@ -293,7 +312,7 @@ int rk_rank2(const float* r, const float* g, const float* y, const float* x, int
 }
 
 static bool valid_opts(const rk_opts& o, int q) {
-    return omega_ok(o.omega, q) && o.check_every >= 0 && o.round0 >= 0 &&
+    return omega_ok(o.omega, q) && sampling_ok(o) && o.check_every >= 0 && o.round0 >= 0 &&
            o.timeout_s > 0.0 && !(o.criterion == 1 && !o.x_ref) && o.criterion >= 0 &&
            o.criterion <= 1 &&
            (o.lookahead == 0 || o.lookahead == 1 || o.lookahead == 2 || o.lookahead == 4 ||

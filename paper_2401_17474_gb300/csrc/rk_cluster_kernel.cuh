@@ -169,10 +169,14 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
         for (int64_t base = 0; base < total_ && !stop; base += 32) {
             const int64_t tl = base + lane_;
             if (tl < total_) {
-                const uint32_t row = sample_row(p.seed, worker, p.stream_id, tbase + (uint64_t)tl, p.m,
-                                                p.thr64, p.alias);
+                uint32_t row = draw_row(p, worker, tbase + (uint64_t)tl);
+                if (row >= p.m) {   // a row block of zero weight: nothing to draw
+                    set_status(status, RK_EINVAL);
+                    row = 0;
+                }
                 const float sc = (ELT == ELT_FP8) ? __ldg(p.row_scale + row) : 1.f;
-                pbuf[lane_] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row), sc);
+                const float wi = p.row_weight ? __ldg(p.row_weight + row) : 1.f;
+                pbuf[lane_] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row) * wi, sc);
             }
             __syncwarp();
             if (lane_ == 0) {

@@ -64,7 +64,8 @@ extern "C" int rkab_solve_noalloc(const rk_plan* plan, const float* b, const flo
     if (opts) o = *opts;
     if (!omega_ok(o.omega, q) || o.check_every < 0 || o.round0 < 0 ||
         !(o.timeout_s > 0.0) || (o.criterion == 1 && !o.x_ref) || o.criterion < 0 ||
-        o.criterion > 1)
+        o.criterion > 1 || o.sampling < RK_SAMPLE_FULL || o.sampling > RK_SAMPLE_CYCLIC ||
+        (o.sampling != RK_SAMPLE_FULL && o.same_stream))
         return RK_EINVAL;
     void* scratch = nullptr;
     const int rc0 = scratch_address(&scratch);

@@ -195,6 +195,8 @@ int run_refine(const Plan* lowp, const float* A32, int64_t lda32, const float* b
         io.stream_id = 3u + ((uint32_t)outer << 8);
         io.timeout_s = o.timeout_s;
         io.lookahead = o.lookahead;
+        io.sampling = o.sampling;
+        io.row_weight = o.row_weight;
         a.opts = io;
         a.info = static_cast<SolveInfo*>(w.solve_ws);
         a.ldv = (n + 3) / 4 * 4;

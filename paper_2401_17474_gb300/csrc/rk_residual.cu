@@ -68,14 +68,35 @@ __global__ void __launch_bounds__(kResThreads) residual_rows_kernel(
     __shared__ double s_rr[kResThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n4 = n >> 2;
+    // x as float4 when it is 16-byte aligned (the rows always are)
+    const float4* x4 = ((reinterpret_cast<uintptr_t>(x) & 15u) == 0) ? reinterpret_cast<const float4*>(x) : nullptr;
     double rr = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * (kResThreads / 32) + warp; i < m;
          i += (int64_t)gridDim.x * (kResThreads / 32)) {
         const float* a = A + i * lda;
         const float4* a4 = reinterpret_cast<const float4*>(a);
         float hi = 0.f, lo = 0.f;
-        for (int64_t c = lane; c < n4; c += 32) {
-            const float4 v = __ldcs(a4 + c);   // streamed once: evict first
+        int64_t c = lane;
+        if (x4) {
+            // four float4 of the row in flight per lane (streamed once: evict first)
+            for (; c + 96 < n4; c += 128) {
+                float4 v[4], xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    v[u] = __ldcs(a4 + c + 32 * u);
+                    xv[u] = __ldg(x4 + c + 32 * u);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    df_acc(hi, lo, v[u].x, xv[u].x);
+                    df_acc(hi, lo, v[u].y, xv[u].y);
+                    df_acc(hi, lo, v[u].z, xv[u].z);
+                    df_acc(hi, lo, v[u].w, xv[u].w);
+                }
+            }
+        }
+        for (; c < n4; c += 32) {
+            const float4 v = __ldcs(a4 + c);
             const int64_t j = c * 4;
             df_acc(hi, lo, v.x, __ldg(x + j));
             df_acc(hi, lo, v.y, __ldg(x + j + 1));

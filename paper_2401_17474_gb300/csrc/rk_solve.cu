@@ -154,6 +154,9 @@ static KParams base_params(const SolveArgs& a) {
     p.chkpart = a.V + (size_t)(a.q + 1) * (size_t)a.ldv;
     p.vrows = a.q;
     p.jacobi = 0;
+    p.sampling = a.opts.sampling;
+    p.P = pl->ws.P;
+    p.row_weight = a.opts.row_weight;
     p.q = a.q;
     p.alpha = a.alpha;
     p.rounds = a.rounds;
@@ -267,6 +270,36 @@ int launch_solve(const SolveArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return RK_ECUDA;
     count_launch();
     return RK_OK;
+}
+
+// Draws of one worker under any row selection (the draw_row of the solve kernels).
+__global__ void sample_indices_ex_kernel(const KParams p, uint32_t worker, uint64_t t0, int64_t count,
+                                         uint32_t* out) {
+    if (p.setup->status != 0) return;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+         k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = draw_row(p, worker, t0 + (uint64_t)k);
+}
+
+int launch_sample_indices_ex(const Plan* plan, uint64_t seed, uint32_t worker, uint32_t q,
+                             uint32_t stream_id, int sampling, uint64_t t0, int64_t count,
+                             uint32_t* out, cudaStream_t st) {
+    if (count <= 0) return RK_OK;
+    KParams p{};
+    p.m = (uint64_t)plan->m;
+    p.seed = seed;
+    p.stream_id = stream_id;
+    p.thr64 = plan->ws.thr64;
+    p.alias = plan->ws.alias;
+    p.q = (int)q;
+    p.sampling = sampling;
+    p.P = plan->ws.P;
+    p.setup = plan->ws.info;
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    sample_indices_ex_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, worker, t0, count, out);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
 }
 
 int launch_sample_indices(const Plan* plan, uint64_t seed, uint32_t worker, uint32_t stream_id,

@@ -67,6 +67,9 @@ struct KParams {
     int64_t ldv;
     float* chkpart;         // gridDim.x float4: per-CTA check partials of its x slice
     int vrows;              // rows of V holding displacements (averaged, divided by q)
+    int sampling;           // rk_sampling: full law, per-worker row blocks, cyclic
+    const uint64_t* P;      // exclusive prefix of the integer weights (row blocks)
+    const float* row_weight;  // per-row weights w_i (NULL: 1)
     int jacobi;             // RKA with q workers spread over the CTAs (alpha = 1): CTA g
                             // holds workers [g q / G, (g+1) q / G), each one projection per
                             // round from the round's x; their sum is the CTA's row of V
@@ -89,6 +92,34 @@ struct KParams {
     uint32_t row_bytes;     // bytes moved per row (multiple of 16)
     uint32_t stage_stride;  // bytes between stages in shared memory
 };
+
+// Row of worker `worker` (of q) at projection counter t under the sampling mode:
+// the alias draw of the full law; the Distributed Approach's block draw (Philox
+// words as for the alias draw; c = floor(u T_g / 2^64) picks the row whose prefix
+// interval [P_i, P_i + K_i) holds P_start + c, found by bisection; returns m for a
+// block of zero weight); or the cyclic sweep from the block's first row.
+__device__ __forceinline__ uint32_t draw_row(const KParams& p, uint32_t worker, uint64_t t) {
+    if (p.sampling == RK_SAMPLE_FULL)
+        return sample_row(p.seed, worker, p.stream_id, t, p.m, p.thr64, p.alias);
+    const uint64_t q = (uint64_t)p.q, g = worker;
+    const uint64_t start = (g * p.m) / q, end = ((g + 1) * p.m) / q;
+    if (p.sampling == RK_SAMPLE_CYCLIC) return (uint32_t)((start + t) % p.m);
+    const uint64_t ps = __ldg(p.P + start);
+    const uint64_t pe = end == p.m ? p.setup->T : __ldg(p.P + end);
+    const uint64_t tg = pe - ps;
+    if (tg == 0 || end <= start) return (uint32_t)p.m;
+    const U4 r = philox10(U4{(uint32_t)t, (uint32_t)(t >> 32), worker, p.stream_id},
+                          (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+    const uint64_t u = (uint64_t)r.x | ((uint64_t)r.y << 32);
+    const uint64_t target = ps + __umul64hi(u, tg);
+    uint64_t lo = start, hi = end - 1;   // the largest i in the block with P_i <= target
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(p.P + mid) <= target) lo = mid;
+        else hi = mid - 1;
+    }
+    return (uint32_t)lo;
+}
 
 // Projections a CTA makes per round: alpha, or with JAC its share of the q workers
 // (CTA g holds workers [g q / G, (g+1) q / G)).
@@ -207,9 +238,15 @@ __device__ void producer_loop(const KParams& p, uint8_t* stages, uint64_t* full,
                 wk = p.same_stream ? 0u : w0 + (uint32_t)(tl % per);
                 tt = (uint64_t)p.round0 + (uint64_t)(tl / per);
             }
-            const uint32_t row = sample_row(p.seed, wk, p.stream_id, tt, p.m, p.thr64, p.alias);
+            uint32_t row = draw_row(p, wk, tt);
+            if (row >= p.m) {   // a row block of zero weight: nothing to draw
+                set_status(&p.info->status, RK_EINVAL);
+                row = 0;
+            }
             const float sc = (ELT == ELT_FP8) ? __ldg(p.row_scale + row) : 1.f;
-            pbuf[lane] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row), sc);
+            // a per-row weight w_i scales the projection with 1/||A_i||^2
+            const float wi = p.row_weight ? __ldg(p.row_weight + row) : 1.f;
+            pbuf[lane] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row) * wi, sc);
         }
         __syncwarp();
         // ... and one lane moves them, in order, into the ring of stages

@@ -311,3 +311,65 @@ def test_rka_many_workers_matches_oracle(rk, mult, extra, omega):
     x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(200), q=q, alpha=1, rounds=15,
                       seed=9, tab=tab, omega=omega)
     assert _rel(x.cpu().numpy(), x_o) < TOL
+
+
+@pytest.mark.parametrize("sampling", ["blocks", "cyclic"])
+def test_selection_draws_bit_exact(rk, sampling):
+    """Row blocks (Section 3.3.1) and cyclic sweep: the device row choices equal the
+    oracle's for workers of uneven blocks, including a zero row."""
+    s = rk_inputs.gaussian_system(1003, 16, seed=5, row_scale_decades=2.0)
+    A_np = s.A.copy()
+    A_np[17] = 0.0
+    tab = oracle.table(A_np)
+    plan = rk.rk_setup(_padded(A_np, rk))
+    for q, g in ((1, 0), (7, 0), (7, 3), (7, 6), (64, 63)):
+        got = rk.rk_sample_indices(plan, 21, g, 1000, 3000, sampling=sampling, q=q).cpu().numpy()
+        ref = oracle.sample_rows(tab, 21, g, 1000, 3000, sampling=sampling, q=q)
+        assert np.array_equal(got.astype(np.int64) & 0xFFFFFFFF, ref), (q, g)
+
+
+@pytest.mark.parametrize("sampling,q,alpha,rounds", [("blocks", 4, 50, 6), ("cyclic", 3, 40, 5),
+                                                     ("blocks", 1, 30, 4)])
+def test_selection_solve_matches_oracle(rk, sampling, q, alpha, rounds):
+    s = rk_inputs.gaussian_system(2000, 100, seed=0)
+    tab = oracle.table(s.A)
+    plan = rk.rk_setup(_padded(s.A, rk))
+    x, info = rk.rkab_solve(plan, _dev(s.b), q=q, alpha=alpha, rounds=rounds, seed=7,
+                            check_every=0, sampling=sampling)
+    assert info.status == 0
+    x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=q, alpha=alpha, rounds=rounds,
+                      seed=7, tab=tab, sampling=sampling)
+    assert _rel(x.cpu().numpy(), x_o) < TOL
+
+
+def test_row_weights_and_many_worker_blocks_match_oracle(rk):
+    """Per-row weights w_i of Eq. (rka_eq), and RKA with row blocks for more workers than
+    SMs (the workers spread over the CTAs)."""
+    s = rk_inputs.gaussian_system(4000, 100, seed=3)
+    tab = oracle.table(s.A)
+    plan = rk.rk_setup(_padded(s.A, rk))
+    w = np.random.default_rng(1).uniform(0.5, 1.5, 4000).astype(np.float32)
+    x, info = rk.rkab_solve(plan, _dev(s.b), q=5, alpha=40, rounds=5, seed=2, check_every=0,
+                            row_weight=_dev(w))
+    x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=5, alpha=40, rounds=5, seed=2,
+                      tab=tab, row_weight=w.astype(np.float64))
+    assert info.status == 0 and _rel(x.cpu().numpy(), x_o) < TOL
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    q = 2 * sms + 5
+    x, info = rk.rka_solve(plan, _dev(s.b), q=q, rounds=10, seed=4, check_every=0, sampling="blocks")
+    x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=q, alpha=1, rounds=10, seed=4,
+                      tab=tab, sampling="blocks")
+    assert info.status == 0 and _rel(x.cpu().numpy(), x_o) < TOL
+
+
+def test_zero_weight_block_is_refused(rk):
+    """A worker whose row block has no weight cannot draw: the solve ends with RK_EINVAL."""
+    s = rk_inputs.gaussian_system(400, 20, seed=1)
+    A_np = s.A.copy()
+    A_np[100:200] = 0.0                      # block 1 of 4
+    plan = rk.rk_setup(_padded(A_np, rk))
+    with pytest.raises(rk.RkError) as e:
+        rk.rkab_solve(plan, _dev(s.b), q=4, alpha=10, rounds=3, seed=0, sampling="blocks")
+    assert e.value.code == -1
+    with pytest.raises(rk.RkError):
+        rk.rkab_solve(plan, _dev(s.b), q=4, alpha=10, rounds=1, sampling="blocks", same_stream=True)

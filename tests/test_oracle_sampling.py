@@ -161,3 +161,84 @@ def test_sampler_streams_are_distinct_and_reproducible():
     # a window of the stream equals the same window drawn from its own start
     assert np.array_equal(oracle.sample_rows(tab, 9, 0, 700, 300), s0[700:1000])
     assert s0.min() >= 0 and s0.max() < 500
+
+
+# --------------------------------------------------------------------------
+# Row selections other than the whole law: the Distributed Approach's row blocks
+# (Section 3.3.1) and the cyclic sweep (Section 2.1)
+# --------------------------------------------------------------------------
+def _blocks(m, q):
+    return [((g * m) // q, ((g + 1) * m) // q) for g in range(q)]
+
+
+def test_block_draws_follow_the_block_law():
+    """Worker g of q draws only inside rows [g m/q, (g+1) m/q), with probability
+    ||a_i||^2 / (block sum): chi-square of 2e5 draws against exact rational norms."""
+    rng = np.random.default_rng(4)
+    m, n, q = 37, 6, 4                         # blocks of unequal size
+    A = (rng.standard_normal((m, n)) * rng.uniform(0.1, 3.0, size=(m, 1))).astype(np.float32)
+    A[5] = 0.0                                  # a zero row is never drawn
+    tab = oracle.table(A)
+    w = np.array([float(sum(Fraction(float(v)) ** 2 for v in row)) for row in A])
+    for g, (s0, s1) in enumerate(_blocks(m, q)):
+        d = oracle.sample_rows(tab, 11, g, 0, 200_000, sampling="blocks", q=q)
+        assert d.min() >= s0 and d.max() < s1
+        assert 5 not in set(d.tolist())
+        p = w[s0:s1] / w[s0:s1].sum()
+        cnt = np.bincount(d - s0, minlength=s1 - s0)
+        keep = p > 0
+        chi2 = float((((cnt - 200_000 * p) ** 2)[keep] / (200_000 * p[keep])).sum())
+        dof = int(keep.sum()) - 1
+        assert chi2 < dof + 6 * np.sqrt(2 * dof), (g, chi2, dof)
+
+
+def test_one_block_is_the_whole_law():
+    """q = 1: the single block is the whole matrix, so the block draw follows Eq.
+    (prob_line) (same law as the alias draw, from other arithmetic)."""
+    s = rk_inputs.gaussian_system(50, 5, seed=8, row_scale_decades=1.0)
+    tab = oracle.table(s.A)
+    d = oracle.sample_rows(tab, 2, 0, 0, 300_000, sampling="blocks", q=1)
+    e = oracle.sample_rows(tab, 2, 0, 300_000, 300_000)
+    p = tab.K.astype(np.float64) / float(tab.T)
+    for draws in (d, e):
+        cnt = np.bincount(draws, minlength=50)
+        chi2 = float(((cnt - 300_000 * p) ** 2 / (300_000 * p)).sum())
+        assert chi2 < 49 + 6 * np.sqrt(98)
+
+
+def test_cyclic_sweep_order():
+    """Cyclic selection: worker g of q takes rows g m/q, g m/q + 1, ... modulo m."""
+    s = rk_inputs.gaussian_system(23, 4, seed=1)
+    tab = oracle.table(s.A)
+    for g, q in ((0, 1), (1, 3), (2, 3)):
+        start = (g * 23) // q
+        got = oracle.sample_rows(tab, 0, g, 5, 40, sampling="cyclic", q=q)
+        assert np.array_equal(got, (start + 5 + np.arange(40)) % 23)
+
+
+def test_row_weights_equal_uniform_relaxation():
+    """Eq. (rka_eq) with w_i = c for every row is the uniform relaxation c; w_i = 1 is
+    the unweighted method (both bit for bit: the product omega w_i is exact)."""
+    s = rk_inputs.gaussian_system(200, 10, seed=2)
+    tab = oracle.table(s.A)
+    b = s.b.astype(np.float64)
+    x1 = oracle.rkab(s.A, b, np.zeros(10), q=3, alpha=20, rounds=5, seed=4, tab=tab,
+                     row_weight=np.ones(200))
+    x2 = oracle.rkab(s.A, b, np.zeros(10), q=3, alpha=20, rounds=5, seed=4, tab=tab)
+    assert np.array_equal(x1, x2)
+    x3 = oracle.rkab(s.A, b, np.zeros(10), q=3, alpha=20, rounds=5, seed=4, tab=tab,
+                     row_weight=np.full(200, 0.5))
+    x4 = oracle.rkab(s.A, b, np.zeros(10), q=3, alpha=20, rounds=5, seed=4, tab=tab, omega=0.5)
+    assert np.array_equal(x3, x4)
+
+
+@pytest.mark.parametrize("sampling", ["blocks", "cyclic"])
+def test_other_selections_converge(sampling):
+    """Consistent 400 x 20 system: RKAB with row blocks (each block of 100 rows keeps
+    full column rank) and cyclic Kaczmarz (q = 1) converge to x*."""
+    s = rk_inputs.gaussian_system(400, 20, seed=6)
+    tab = oracle.table(s.A)
+    q = 4 if sampling == "blocks" else 1
+    x = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(20), q=q, alpha=100, rounds=60,
+                    seed=1, tab=tab, sampling=sampling)
+    assert np.linalg.norm(x - s.x_star) / np.linalg.norm(s.x_star) < 1e-5
