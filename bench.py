@@ -69,12 +69,13 @@ def parse():
                     help="relaxation of the timed solve: a number, or 'star' for alpha* of "
                          "Eq. (best_alpha) from the GPU spectrum estimate (computed before timing)")
     ap.add_argument("--workload", default="consistent",
-                    choices=["consistent", "lsq", "precision", "horizon"],
+                    choices=["consistent", "lsq", "precision", "horizon", "adjoint"],
                     help="consistent: 80000 x 10000 to 1e-6 (default); lsq: 200000 x 20000 "
                          "row-scaled inconsistent system, budget of rounds with the normal-equation "
                          "criterion logged every round; precision: 1e6 x 16000, FP32 vs BF16/FP8 "
                          "+ refinement to 1e-6; horizon: 80000 x 1000 inconsistent system, error "
-                         "to x_LS and residual along RKA / RKAB runs for several worker counts")
+                         "to x_LS and residual along RKA / RKAB runs for several worker counts; "
+                         "adjoint: backward pass of the least-squares solve at 200000 x 20000")
     return ap.parse_args()
 
 
@@ -650,6 +651,56 @@ def run_horizon(args, rk, dev):
     return line
 
 
+def run_adjoint_large(args, rk, dev):
+    """Differentiation form at 200000 x 20000 (b = A x* + N(0, 1e-3^2), L = 0.5||x - x_t||^2):
+    forward RKA with alpha* (4864 workers), then the backward pass -- A^T copy and its
+    plan, the minimum-norm solve on A^T (rows of 800 KB: 16-CTA cluster workers with
+    relaxation), the solve of A g = y (RKA with alpha*), the residual and the rank-2
+    gradient of A.  The relative residuals of both solves are reported with the times."""
+    import torch
+
+    import rk_inputs
+    m, n = 200000, 20000
+    A, b, _ = rk_inputs.gaussian_system_torch(m, n, seed=args.seed, noise=1e-3, device=str(dev))
+    xt = torch.randn(n, generator=torch.Generator(device=dev).manual_seed(5), device=dev)
+    plan = rk.rk_setup(A)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    qa = 32 * sms
+    omega_a, sp = rk.optimal_weight(A, qa, k=4)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    e[0].record()
+    x, info_f = rk.rka_solve(plan, b, q=qa, rounds=150, seed=args.seed, omega=omega_a,
+                             check_every=0)
+    e[1].record()
+    cfg = rk.AdjointConfig(q=qa, alpha=1, rounds=150, omega=omega_a, q_t=6, cluster_size_t=16,
+                           alpha_t=4000, rounds_t=40, omega_t=2.0, seed=args.seed + 1)
+    e[2].record()
+    adj = rk.Adjoint(plan, cfg)
+    e[3].record()
+    gx = x - xt
+    grad_A, grad_b, g = adj.backward(b, x, gx)
+    e[4].record()
+    torch.cuda.synchronize(dev)
+    t_fwd, t_setup, t_bwd = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3]), e[3].elapsed_time(e[4])
+    # accuracy of the two solves: ||A^T y - gx|| / ||gx|| and ||A g - y|| / ||y||
+    _, nt = rk.rk_residual(adj.At, gx, grad_b, want_atr=False)
+    _, na = rk.rk_residual(A, grad_b, g, want_atr=False)
+    res_t = float(nt[0]) / float(torch.linalg.norm(gx))
+    res_a = float(na[0]) / float(torch.linalg.norm(grad_b))
+    line = _base_line(args, METRIC, 0.0, UNIT, t_fwd + t_setup + t_bwd, {
+        "workload": f"lstsq_adjoint_{m}x{n}", "m": m, "n": n,
+        "forward": {"method": f"RKA q={qa} alpha*={omega_a:.1f}", "rounds": 150, "ms": round(t_fwd, 2)},
+        "transpose_and_plan_ms": round(t_setup, 2),
+        "backward_ms": round(t_bwd, 2),
+        "y_solve": {"on": "A^T (20000 rows of 200000)", "q": 6, "cluster": 16, "alpha": 4000,
+                    "rounds": 40, "omega": 2.0, "relative_residual": res_t},
+        "g_solve": {"q": qa, "alpha": 1, "rounds": 150, "omega": round(omega_a, 2),
+                    "relative_residual": res_a},
+        "grad_A_bytes": m * n * 4,
+        "note": "value unused: this workload times one backward pass"}, None, None)
+    return line
+
+
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
@@ -671,7 +722,8 @@ def run_ours(args):
 
     if args.workload != "consistent":
         if rank == 0:
-            fn = {"lsq": run_lsq, "precision": run_precision, "horizon": run_horizon}[args.workload]
+            fn = {"lsq": run_lsq, "precision": run_precision, "horizon": run_horizon,
+                  "adjoint": run_adjoint_large}[args.workload]
             print(json.dumps(fn(args, rk, dev)), flush=True)
         if ws > 1:
             import torch.distributed as dist

@@ -301,21 +301,21 @@ int rk_rank2(const float *r, const float *g, const float *y, const float *x, int
              float *G, int64_t ldg, void *stream);
 
 /* Bytes of device workspace rkab_adjoint needs. */
-size_t rk_adjoint_workspace_bytes(const rk_plan *plan_A, const rk_plan *plan_At, int q);
+size_t rk_adjoint_workspace_bytes(const rk_plan *plan_A, const rk_plan *plan_At, int q_t, int q);
 
 /* Backward pass of the least-squares solve at the point x (device, n floats):
  *   plan_A   float32 plan of A (m x n); plan_At float32 plan of A^T (n x m, e.g. from
  *            rk_transpose); both must outlive the call
  *   b        device, m floats;  gx device, n floats: dL/dx at x
- *   y-solve  RKAB on A^T y = gx from y = 0: q workers, alpha_t, rounds_t, opts_t (Philox
- *            stream id 1; cluster_size and lookahead are honoured)
- *   g-solve  RKAB on A g = y from g = 0: q, alpha, rounds, opts (stream id 2)
+ *   y-solve  RKAB on A^T y = gx from y = 0: q_t workers, alpha_t, rounds_t, opts_t
+ *            (Philox stream id 1; omega, cluster_size, lookahead and sampling honoured)
+ *   g-solve  RKAB on A g = y from g = 0: q workers, alpha, rounds, opts (stream id 2)
  *   grad_b   device, m floats <- y;  g device, n floats <- g
  *   grad_A   device, m x n (ldg) <- r g^T - y x^T with r = b - A x (float64-accumulated)
  * Synchronises `stream` at the end and returns RK_OK or the first error (device status of
  * either solve included). */
 int rkab_adjoint(const rk_plan *plan_A, const rk_plan *plan_At, const float *b, const float *x,
-                 const float *gx, int q, int64_t alpha_t, int64_t rounds_t, int64_t alpha,
+                 const float *gx, int q_t, int q, int64_t alpha_t, int64_t rounds_t, int64_t alpha,
                  int64_t rounds, uint64_t seed, const rk_opts *opts_t, const rk_opts *opts,
                  float *grad_b, float *g, float *grad_A, int64_t ldg, void *workspace,
                  size_t ws_bytes, void *stream);

@@ -85,8 +85,9 @@ _SIG = {
                                     ctypes.c_int64, _V]),
     "rk_rank2": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_int64, ctypes.c_int64, _V, ctypes.c_int64,
                                 _V]),
-    "rk_adjoint_workspace_bytes": (ctypes.c_size_t, [_V, _V, ctypes.c_int]),
-    "rkab_adjoint": (ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+    "rk_adjoint_workspace_bytes": (ctypes.c_size_t, [_V, _V, ctypes.c_int, ctypes.c_int]),
+    "rkab_adjoint": (ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                    ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
                                     ctypes.POINTER(RkOpts), ctypes.POINTER(RkOpts), _V, _V, _V,
                                     ctypes.c_int64, _V, ctypes.c_size_t, _V]),

@@ -408,7 +408,7 @@ def rank2(r, g, y, x, out=None, stream=None) -> torch.Tensor:
 @dataclass
 class AdjointConfig:
     """Parameters of the two solves of the backward pass."""
-    q: int = 8
+    q: int = 8                # workers of the solve of A g = y
     alpha_t: int = 0          # projections per worker per round on A^T (0: its row count n)
     rounds_t: int = 40
     alpha: int = 0            # projections per worker per round on A g = y (0: n)
@@ -417,6 +417,9 @@ class AdjointConfig:
     cluster_size_t: int = 0   # CTAs per worker on A^T (long rows of length m)
     cluster_size: int = 0
     lookahead: int = 0
+    q_t: int = 0              # workers of the solve on A^T (0: q)
+    omega_t: float = 1.0      # relaxation of the solve on A^T
+    omega: float = 1.0        # relaxation of the solve of A g = y
 
 
 class Adjoint:
@@ -427,7 +430,8 @@ class Adjoint:
         self.cfg = cfg
         self.At = transpose(plan_A.A, stream)
         self.plan_At = Plan(self.At, "f32", None, stream)
-        nbytes = _lib.load().rk_adjoint_workspace_bytes(plan_A.handle, self.plan_At.handle, cfg.q)
+        nbytes = _lib.load().rk_adjoint_workspace_bytes(plan_A.handle, self.plan_At.handle,
+                                                        cfg.q_t or cfg.q, cfg.q)
         if nbytes == 0:
             raise RkError(_lib.RK_EINVAL, "rk_adjoint_workspace_bytes")
         self.ws = _workspace(nbytes, plan_A.device)
@@ -441,10 +445,13 @@ class Adjoint:
         g = torch.empty(n, dtype=torch.float32, device=dev)
         ldg = (n + 3) // 4 * 4
         grad_A = torch.empty((m, ldg), dtype=torch.float32, device=dev)[:, :n]
-        ot = make_opts(check_every=0, cluster_size=c.cluster_size_t, lookahead=c.lookahead)
-        oa = make_opts(check_every=0, cluster_size=c.cluster_size, lookahead=c.lookahead)
+        ot = make_opts(omega=c.omega_t, check_every=0, cluster_size=c.cluster_size_t,
+                       lookahead=c.lookahead)
+        oa = make_opts(omega=c.omega, check_every=0, cluster_size=c.cluster_size,
+                       lookahead=c.lookahead)
         check(_lib.load().rkab_adjoint(self.plan_A.handle, self.plan_At.handle, _ptr(b), _ptr(x),
-                                       _ptr(gx), c.q, c.alpha_t or n, c.rounds_t, c.alpha or n,
+                                       _ptr(gx), c.q_t or c.q, c.q, c.alpha_t or n, c.rounds_t,
+                                       c.alpha or n,
                                        c.rounds, c.seed, ctypes.byref(ot), ctypes.byref(oa),
                                        _ptr(grad_b), _ptr(g), _ptr(grad_A), grad_A.stride(0),
                                        _ptr(self.ws), self.ws.numel(), _stream(stream)),

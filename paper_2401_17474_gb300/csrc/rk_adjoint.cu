@@ -85,17 +85,17 @@ int launch_rank2(const float* r, const float* g, const float* y, const float* x,
 }
 
 // Workspace: r64 (m doubles) | r32 (m floats) | zeros (max(m, n) floats) |
-//            solve workspace for A^T (q) | solve workspace for A (q) | residual workspace
-size_t adjoint_ws_bytes(const Plan* pa, const Plan* pt, int q) {
+//            solve workspace for A^T (q_t) | solve workspace for A (q) | residual workspace
+size_t adjoint_ws_bytes(const Plan* pa, const Plan* pt, int q_t, int q) {
     const int64_t m = pa->m, n = pa->n;
     const int64_t zn = (m > n ? m : n) + 4;
     return align256((size_t)m * 8) + align256((size_t)m * 4) + align256((size_t)zn * 4) +
-           align256(solve_ws_bytes(pt, q)) + align256(solve_ws_bytes(pa, q)) +
+           align256(solve_ws_bytes(pt, q_t)) + align256(solve_ws_bytes(pa, q)) +
            align256(residual_ws_bytes(m, n));
 }
 
 int run_adjoint(const Plan* pa, const Plan* pt, const float* b, const float* x, const float* gx,
-                int q, int64_t alpha_t, int64_t rounds_t, int64_t alpha, int64_t rounds, uint64_t seed,
+                int q_t, int q, int64_t alpha_t, int64_t rounds_t, int64_t alpha, int64_t rounds, uint64_t seed,
                 const rk_opts& ot, const rk_opts& oa, float* grad_b, float* grad_A, int64_t ldg,
                 float* g_out, void* ws, cudaStream_t st) {
     const int64_t m = pa->m, n = pa->n;
@@ -108,7 +108,7 @@ int run_adjoint(const Plan* pa, const Plan* pt, const float* b, const float* x, 
     const int64_t zn = (m > n ? m : n) + 4;
     p += align256((size_t)zn * 4);
     void* wt = p;
-    p += align256(solve_ws_bytes(pt, q));
+    p += align256(solve_ws_bytes(pt, q_t));
     void* wa = p;
     p += align256(solve_ws_bytes(pa, q));
     void* wr = p;
@@ -120,7 +120,7 @@ int run_adjoint(const Plan* pa, const Plan* pt, const float* b, const float* x, 
     s1.b = gx;
     s1.x0 = zeros;
     s1.x = grad_b;
-    s1.q = q;
+    s1.q = q_t;
     s1.alpha = alpha_t;
     s1.rounds = rounds_t;
     s1.seed = seed;
@@ -140,6 +140,7 @@ int run_adjoint(const Plan* pa, const Plan* pt, const float* b, const float* x, 
     s2.b = grad_b;
     s2.x0 = zeros;
     s2.x = g_buf;
+    s2.q = q;
     s2.alpha = alpha;
     s2.rounds = rounds;
     s2.opts = oa;

@@ -320,18 +320,18 @@ static bool valid_opts(const rk_opts& o, int q) {
            o.cluster_size >= 0 && o.cluster_size <= 16 && (o.cluster_size & (o.cluster_size - 1)) == 0;
 }
 
-size_t rk_adjoint_workspace_bytes(const rk_plan* plan_A, const rk_plan* plan_At, int q) {
-    if (!plan_A || !plan_At || q < 1) return 0;
-    return adjoint_ws_bytes(&plan_A->p, &plan_At->p, q);
+size_t rk_adjoint_workspace_bytes(const rk_plan* plan_A, const rk_plan* plan_At, int q_t, int q) {
+    if (!plan_A || !plan_At || q < 1 || q_t < 1) return 0;
+    return adjoint_ws_bytes(&plan_A->p, &plan_At->p, q_t, q);
 }
 
 int rkab_adjoint(const rk_plan* plan_A, const rk_plan* plan_At, const float* b, const float* x,
-                 const float* gx, int q, int64_t alpha_t, int64_t rounds_t, int64_t alpha,
+                 const float* gx, int q_t, int q, int64_t alpha_t, int64_t rounds_t, int64_t alpha,
                  int64_t rounds, uint64_t seed, const rk_opts* opts_t, const rk_opts* opts,
                  float* grad_b, float* g, float* grad_A, int64_t ldg, void* workspace,
                  size_t ws_bytes, void* stream) {
     if (!plan_A || !plan_At || !b || !x || !gx || !grad_b || !g || !grad_A || !workspace ||
-        q < 1 || alpha_t < 1 || rounds_t < 1 || alpha < 1 || rounds < 1)
+        q < 1 || q_t < 1 || alpha_t < 1 || rounds_t < 1 || alpha < 1 || rounds < 1)
         return RK_EINVAL;
     const Plan& pa = plan_A->p;
     const Plan& pt = plan_At->p;
@@ -346,9 +346,9 @@ int rkab_adjoint(const rk_plan* plan_A, const rk_plan* plan_At, const float* b, 
     if (opts) oa = *opts;
     ot.criterion = 0;
     oa.criterion = 0;
-    if (!valid_opts(ot, q) || !valid_opts(oa, q)) return RK_EINVAL;
-    if (ws_bytes < adjoint_ws_bytes(&pa, &pt, q)) return RK_EWORKSPACE;
-    return run_adjoint(&pa, &pt, b, x, gx, q, alpha_t, rounds_t, alpha, rounds, seed, ot, oa,
+    if (!valid_opts(ot, q_t) || !valid_opts(oa, q)) return RK_EINVAL;
+    if (ws_bytes < adjoint_ws_bytes(&pa, &pt, q_t, q)) return RK_EWORKSPACE;
+    return run_adjoint(&pa, &pt, b, x, gx, q_t, q, alpha_t, rounds_t, alpha, rounds, seed, ot, oa,
                        grad_b, grad_A, ldg, g, workspace, static_cast<cudaStream_t>(stream));
 }
 

@@ -7,6 +7,7 @@ namespace rk {
 static const ClusterVariant kTab[] = {
     V_(128, 2, 4), V_(128, 3, 4), V_(128, 5, 4), V_(128, 8, 4),
     V_(128, 2, 6), V_(128, 3, 6), V_(128, 5, 6), V_(128, 8, 6),
+    V_(256, 6, 2), V_(256, 9, 2), V_(256, 13, 2),
 };
 #undef V_
 

@@ -116,9 +116,9 @@ int launch_transpose(const float* A, int64_t m, int64_t n, int64_t lda, float* A
                      cudaStream_t st);
 int launch_rank2(const float* r, const float* g, const float* y, const float* x, int64_t m, int64_t n,
                  float* G, int64_t ldg, cudaStream_t st);
-size_t adjoint_ws_bytes(const Plan* pa, const Plan* pt, int q);
+size_t adjoint_ws_bytes(const Plan* pa, const Plan* pt, int q_t, int q);
 int run_adjoint(const Plan* pa, const Plan* pt, const float* b, const float* x, const float* gx,
-                int q, int64_t alpha_t, int64_t rounds_t, int64_t alpha, int64_t rounds, uint64_t seed,
+                int q_t, int q, int64_t alpha_t, int64_t rounds_t, int64_t alpha, int64_t rounds, uint64_t seed,
                 const rk_opts& ot, const rk_opts& oa, float* grad_b, float* grad_A, int64_t ldg,
                 float* g_out, void* ws, cudaStream_t st);
 

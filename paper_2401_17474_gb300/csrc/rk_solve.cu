@@ -69,13 +69,15 @@ static int launch_cluster_solve(const SolveArgs& a, const KParams& base, int C, 
     const ClusterVariant* tab = pl->dt == RK_F32 ? cluster_variants_f32(&count)
                               : pl->dt == RK_BF16 ? cluster_variants_bf16(&count)
                                                   : cluster_variants_fp8(&count);
-    const int nt = 128;
+    // 128 consumers per CTA up to 1024 slices per chunk; 256 (up to 13 slices each, the
+    // register budget of 9 warps) for the chunks of very long rows
+    const int nt = chunk <= 128 * 8 ? 128 : 256;
     const int need = (chunk + nt - 1) / nt;
     int want_w = a.opts.lookahead > 1 ? a.opts.lookahead : 6;
     const ClusterVariant* var = nullptr;
     uint32_t stride = 0;
     int S = 0;
-    for (int w : {want_w, 6, 4}) {
+    for (int w : {want_w, 6, 4, 2}) {
         const ClusterVariant* best = nullptr;
         for (int i = 0; i < count; ++i)
             if (tab[i].nt == nt && tab[i].w == w && tab[i].vpt >= need && (!best || tab[i].vpt < best->vpt))

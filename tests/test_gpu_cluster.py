@@ -34,7 +34,7 @@ def _rel(xg, xo):
                                                 (6000, 10000, 4, 23, 2)])
 def test_cluster_workers_match_oracle(rk, C, lookahead, m, n, q, alpha, rounds):
     chunk = -(-(-(-n // 4) // C) // 4) * 4          # slices per CTA
-    if 4 * C > (n + 3) // 4 or chunk > 128 * 8:
+    if 4 * C > (n + 3) // 4 or chunk > 256 * 13:
         pytest.skip("no cluster shape for this row length")
     s = rk_inputs.gaussian_system(m, n, seed=m + n + C)
     plan = rk.rk_setup(rk.aligned_rows(_dev(s.A)))
@@ -72,3 +72,18 @@ def test_cluster_rk_converges_with_stop_rule(rk):
                             tol=1e-6, cluster_size=8)
     assert info.status == 0 and info.last_metric < 1e-6, info
     assert _rel(x.cpu().numpy(), s.x_star.astype(np.float64)) < 1e-6
+
+
+@pytest.mark.parametrize("C", [8, 16])
+def test_long_row_cluster_workers_match_oracle(rk, C):
+    """Rows of 70000 columns (chunks of more than 1024 slices per CTA: the 256-thread
+    cluster variants with look-ahead pairs), an underdetermined consistent system."""
+    m, n, q = 300, 70000, 2
+    s = rk_inputs.gaussian_system(m, n, seed=C)
+    plan = rk.rk_setup(rk.aligned_rows(_dev(s.A)))
+    tab = oracle.table(s.A)
+    x, info = rk.rkab_solve(plan, _dev(s.b), q=q, alpha=40, rounds=3, seed=5, cluster_size=C)
+    assert info.status == 0 and info.rounds_done == 3
+    xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(n), q=q, alpha=40, rounds=3, seed=5,
+                     tab=tab)
+    assert _rel(x.cpu().numpy(), xo) < TOL
