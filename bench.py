@@ -86,6 +86,20 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_totals(total_ms, units, world_size, device):
+    """Whole-job figures of independent replicas: the slowest rank's time and the sum of
+    all ranks' projections (one all-reduce each; the data path itself has no collective)."""
+    if world_size <= 1:
+        return float(total_ms), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -805,15 +819,7 @@ def run_ours(args):
         raise rk.RkError(info.status, "timed solve")
     rounds_t = info.rounds_done
     units = q * alpha * rounds_t * args.steps
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms, float(units)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        total_ms_all, units_all = float(tmax[0]), float(t[1])
-    else:
-        total_ms_all, units_all = total_ms, float(units)
+    total_ms_all, units_all = replica_totals(total_ms, units, ws, dev)
     value = units_all / (total_ms_all / 1e3)
 
     # roofline of the dominant kernel (the persistent solve), from its own events
