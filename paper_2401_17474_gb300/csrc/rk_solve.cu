@@ -236,7 +236,10 @@ int launch_solve(const SolveArgs& a, cudaStream_t st) {
     for (int attempt = 0; attempt < 3; ++attempt) {
         const SolveVariant* v1 = pick_variant(pl->dt, n4, 1, 1, jac);
         if (!v1) return RK_EINVAL;
-        const int wauto = jac ? 1 : ((w == 0) ? (v1->vpt <= 3 ? 4 : 1) : w);
+        // measured: groups of 4 pay off only with a single consumer warp (n <= 512);
+        // from 128 consumers up, one row at a time is faster (0.34 against 0.40 us a
+        // row at n = 1000, 0.43 against 0.63-0.66 at n = 4000)
+        const int wauto = jac ? 1 : ((w == 0) ? (v1->nt == 32 ? 4 : 1) : w);
         var = pick_variant(pl->dt, n4, wauto, 1, jac);
         if (!var) var = v1;
         // stages are padded to the variant's NT * VPT slices (zeroed at kernel start)
