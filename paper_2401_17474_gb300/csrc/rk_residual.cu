@@ -153,9 +153,28 @@ __global__ void __launch_bounds__(kResThreads) residual_atr_kernel(
     if (j0 >= n) return;
     float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f, l3 = 0.f;
     const bool full4 = (j0 + 3 < n);
-#pragma unroll 4
-    for (int64_t i = i0; i < i1; ++i) {
-        const float2 rr = __ldg(rs + i);   // r_i = rh + rl, split once per row
+    int64_t i = i0;
+    if (full4) {
+        // four rows in flight per thread; rows in ascending order as below
+        for (; i + 4 <= i1; i += 4) {
+            float4 v[4];
+            float2 rr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v[u] = __ldcs(reinterpret_cast<const float4*>(A + (i + u) * lda + j0));
+                rr[u] = __ldg(rs + i + u);   // r_i = rh + rl, split once per row
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                df_acc_split(h0, l0, v[u].x, rr[u].x, rr[u].y);
+                df_acc_split(h1, l1, v[u].y, rr[u].x, rr[u].y);
+                df_acc_split(h2, l2, v[u].z, rr[u].x, rr[u].y);
+                df_acc_split(h3, l3, v[u].w, rr[u].x, rr[u].y);
+            }
+        }
+    }
+    for (; i < i1; ++i) {
+        const float2 rr = __ldg(rs + i);
         const float rh = rr.x, rl = rr.y;
         const float* a = A + i * lda + j0;
         if (full4) {
