@@ -180,14 +180,17 @@ int rk_sample_indices_ex(const rk_plan *plan, uint64_t seed, uint32_t worker, ui
 /* sampled rows from HBM into a ring of shared-memory stages.               */
 /* ------------------------------------------------------------------------ */
 
-/* Bytes of device workspace one solve with q workers needs. */
+/* Bytes of device workspace one solve with q workers needs: with r = min(q, twice the SM
+ * count of the current device), about (r + 1) * ceil(n / 4) * 16 + 256 r bytes. */
 size_t rk_solve_workspace_bytes(const rk_plan *plan, int q);
 
 /* Run `rounds` rounds (fewer if the convergence criterion is met).
  *   b          device, m floats
  *   x0         device, n floats: starting point (may alias x)
  *   x          device, n floats: result
- *   q          workers, 1 <= q <= the co-resident CTA limit (RK_ENOTCORESIDENT beyond)
+ *   q          workers: up to twice the SM count (one CTA per worker, two per SM beyond
+ *              the SM count; RK_ENOTCORESIDENT beyond), any q >= 1 for alpha = 1 (RKA:
+ *              more workers than SMs are spread over one CTA per SM)
  *   alpha      projections per worker between averages, >= 1
  *   seed       Philox key
  *   opts       NULL for defaults
@@ -220,7 +223,7 @@ typedef struct {
  *   result   where the outcome is written when the solve ends (stream-ordered): any
  *            address cudaMemcpyAsync accepts (device or pinned host); NULL to skip
  * Returns RK_ETOOLARGE when rk_solve_workspace_bytes(plan, q) exceeds the array
- * (about (q + 1) * ceil(n / 4) * 16 + 256 q bytes; q <= 207 at n = 10000), before any device
+ * (q <= 207 at n = 10000 on 152 SMs; any q for RKA), before any device
  * work.  Every GPU that loads the library holds the array until the process exits.
  * The first call on a device looks up the array's device address with that device
  * current; make that first call before any stream capture.  All calls on a device

@@ -88,6 +88,7 @@ struct SolveArgs {
 int launch_sample_indices_ex(const Plan* plan, uint64_t seed, uint32_t worker, uint32_t q,
                              uint32_t stream_id, int sampling, uint64_t t0, int64_t count,
                              uint32_t* out, cudaStream_t st);
+int v_rows(int q);
 size_t solve_ws_bytes(const Plan* plan, int q);
 int launch_solve(const SolveArgs& a, cudaStream_t st);
 int launch_sample_indices(const Plan* plan, uint64_t seed, uint32_t worker, uint32_t stream_id,

@@ -152,8 +152,9 @@ static KParams base_params(const SolveArgs& a) {
     p.x = a.x;
     p.V = a.V;
     p.ldv = a.ldv;
-    p.xbuf = a.V + (size_t)a.q * (size_t)a.ldv;
-    p.chkpart = a.V + (size_t)(a.q + 1) * (size_t)a.ldv;
+    const int rows = v_rows(a.q);
+    p.xbuf = a.V + (size_t)rows * (size_t)a.ldv;
+    p.chkpart = a.V + (size_t)(rows + 1) * (size_t)a.ldv;
     p.vrows = a.q;
     p.jacobi = 0;
     p.sampling = a.opts.sampling;
@@ -320,13 +321,25 @@ int launch_sample_indices(const Plan* plan, uint64_t seed, uint32_t worker, uint
     return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
 }
 
+// Rows of V a solve with q workers needs: one per CTA that holds displacements --
+// q for one or two workers per SM and for cluster workers (q is then at most twice
+// the SM count), the SM count when RKA spreads more workers over the CTAs.
+int v_rows(int q) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 256;
+    return q < 2 * sms ? q : 2 * sms;
+}
+
 size_t solve_ws_bytes(const Plan* plan, int q) {
     const int64_t n4 = (plan->n + 3) / 4;
     const int64_t ldv = n4 * 4;
-    // status | V (q x ldv) and the average (ldv) | per-CTA check partials (a float4
-    // for each of up to kClusterMax CTAs per worker)
-    return align256(sizeof(SolveInfo)) + align256((size_t)(q + 1) * (size_t)ldv * sizeof(float) +
-                                                  (size_t)q * kClusterMax * 4 * sizeof(float));
+    const int rows = v_rows(q);
+    // status | V (rows x ldv) and the average (ldv) | per-CTA check partials (a float4
+    // for each of up to kClusterMax CTAs per row of V)
+    return align256(sizeof(SolveInfo)) + align256((size_t)(rows + 1) * (size_t)ldv * sizeof(float) +
+                                                  (size_t)rows * kClusterMax * 4 * sizeof(float));
 }
 
 }  // namespace rk

@@ -8,6 +8,11 @@
 // Ritz values lie inside the spectrum, so lambda_min <= est_min and
 // est_max <= lambda_max (up to rounding): with est_min, the weight of
 // Eq. (best_alpha) errs on the small side.
+// A^T A v is applied in one pass over A where the solve kernel can hold a row
+// (n up to 20480): one round of the RKA kernel in which every row is taken once
+// (cyclic selection, q = m workers), with b = 0, unit reciprocal norms and the
+// weight -m, returns v + A^T A v in float32.  Longer rows take the two residual
+// passes (float64-class).
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -182,7 +187,12 @@ struct SpecWs {
     double* w;       // n
     float* vf;       // n
     double* fpart;   // fro partials
-    void* res;       // residual workspace
+    void* res;       // residual workspace (two-pass operator)
+    SetupInfo* sinfo;  // a passed plan status for the one-pass operator
+    float* ones;     // m
+    float* zeros;    // m
+    float* vout;     // n: v + A^T A v
+    void* solve;     // solve workspace of the one-pass operator
 };
 
 static int fro_blocks(int64_t m) {
@@ -213,14 +223,74 @@ static SpecWs spec_carve(void* base, int64_t m, int64_t n, int k) {
     w.fpart = reinterpret_cast<double*>(p);
     p += align256((size_t)fro_blocks(m) * 8);
     w.res = p;
+    p += align256(residual_ws_bytes(m, n));
+    w.sinfo = reinterpret_cast<SetupInfo*>(p);
+    p += 256;
+    w.ones = reinterpret_cast<float*>(p);
+    p += align256((size_t)m * 4);
+    w.zeros = reinterpret_cast<float*>(p);
+    p += align256((size_t)m * 4);
+    w.vout = reinterpret_cast<float*>(p);
+    p += align256((size_t)n * 4);
+    w.solve = p;
     return w;
+}
+
+static size_t one_pass_solve_bytes(int64_t m, int64_t n) {
+    Plan pl{};
+    pl.n = n;
+    pl.m = m;
+    return solve_ws_bytes(&pl, (int)m);
 }
 
 size_t spectrum_ws_bytes(int64_t m, int64_t n, int k) {
     const size_t ldv = (size_t)((n + 31) / 32 * 32);
     return 256 + 2 * align256((size_t)(k + 1) * 8) + align256((size_t)(k + 1) * ldv * 8) +
            align256((size_t)n * 8) + align256((size_t)n * 4) + align256((size_t)fro_blocks(m) * 8) +
-           residual_ws_bytes(m, n);
+           align256(residual_ws_bytes(m, n)) + 256 + 2 * align256((size_t)m * 4) +
+           align256((size_t)n * 4) + one_pass_solve_bytes(m, n);
+}
+
+__global__ void fill_kernel(float* __restrict__ a, int64_t m, float v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+// w = vout - v in float64 (vout = v + A^T A v from the one-pass operator).
+__global__ void diff_kernel(const float* __restrict__ vout, const float* __restrict__ v, int64_t n,
+                            double* __restrict__ w) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        w[j] = (double)vout[j] - (double)v[j];
+}
+
+// w = A^T A v by one round of the RKA kernel over every row (see the head of this
+// file); returns RK_EINVAL when no solve variant holds a row of n columns.
+static int one_pass_normal_matvec(const Plan& pl, const SpecWs& w, int64_t n, cudaStream_t st) {
+    SolveArgs a;
+    a.plan = &pl;
+    a.b = w.zeros;
+    a.x0 = w.vf;
+    a.x = w.vout;
+    a.q = (int)pl.m;
+    a.alpha = 1;
+    a.rounds = 1;
+    a.seed = 0;
+    rk_opts_default(&a.opts);
+    a.opts.omega = -(float)pl.m;   // c_i = m <A_i, v>, averaged over the m workers
+    a.opts.check_every = 0;
+    a.opts.sampling = RK_SAMPLE_CYCLIC;   // worker i takes row i
+    a.info = static_cast<SolveInfo*>(w.solve);
+    a.ldv = (n + 3) / 4 * 4;
+    a.V = reinterpret_cast<float*>(static_cast<uint8_t*>(w.solve) + align256(sizeof(SolveInfo)));
+    if (cudaMemsetAsync(a.info, 0, sizeof(SolveInfo), st) != cudaSuccess) return RK_ECUDA;
+    const int rc = launch_solve(a, st);
+    if (rc != RK_OK) return rc;
+    diff_kernel<<<(unsigned)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048), 256, 0, st>>>(w.vout, w.vf,
+                                                                                              n, w.w);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
 }
 
 static int grid_for(int64_t n) {
@@ -244,11 +314,32 @@ int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint6
     count_launch(3);
     if (cudaGetLastError() != cudaSuccess) return RK_ECUDA;
 
+    // the plan of the one-pass operator: rows of A, unit reciprocal norms, a passed status
+    Plan pl{};
+    pl.A = A;
+    pl.dt = RK_F32;
+    pl.row_scale = nullptr;
+    pl.m = m;
+    pl.n = n;
+    pl.lda = lda;
+    pl.ws.info = w.sinfo;
+    pl.ws.inv = w.ones;
+    if (cudaMemsetAsync(w.sinfo, 0, 256, st) != cudaSuccess) return RK_ECUDA;
+    fill_kernel<<<grid_for(m), kSpThreads, 0, st>>>(w.ones, m, 1.0f);
+    fill_kernel<<<grid_for(m), kSpThreads, 0, st>>>(w.zeros, m, 0.0f);
+    count_launch(2);
+    bool one_pass = m < (int64_t)1 << 31;
+
     std::vector<double> alpha, beta(1, 0.0);   // beta[j] couples steps j-1 and j
     double fro2 = 0.0;
     for (int j = 0; j < k; ++j) {
         // w = A^T A v_j
-        int rc = launch_normal_matvec(A, m, n, lda, w.vf, w.w, w.res, st);
+        int rc = RK_EINVAL;
+        if (one_pass) {
+            rc = one_pass_normal_matvec(pl, w, n, st);
+            if (rc == RK_EINVAL) one_pass = false;   // rows too long for the solve kernel
+        }
+        if (!one_pass) rc = launch_normal_matvec(A, m, n, lda, w.vf, w.w, w.res, st);
         if (rc != RK_OK) return rc;
         // two passes of classical Gram-Schmidt against v_0 .. v_j
         const int cnt = j + 1;
@@ -261,11 +352,15 @@ int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint6
                                                          w.vf);
         count_launch(6);
         double h[4];
+        int solve_status = 0;
         if (cudaMemcpyAsync(&h[0], w.c1 + j, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(&h[1], w.c2 + j, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(&h[2], w.scal, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            (one_pass && cudaMemcpyAsync(&solve_status, w.solve, sizeof(int), cudaMemcpyDeviceToHost,
+                                         st) != cudaSuccess) ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return RK_ECUDA;
+        if (solve_status != 0) return solve_status;
         fro2 = h[3];
         if (!std::isfinite(h[0]) || !std::isfinite(h[2])) return RK_EDIVERGED;
         alpha.push_back(h[0] + h[1]);   // <A^T A v_j, v_j> with the second pass's correction

@@ -24,13 +24,14 @@ def _dev(a):
 
 def test_spectrum_spanning_space(rk):
     """k = n steps span R^n: the Ritz values at the ends are the extreme eigenvalues of
-    A^T A (up to the float32 rounding of the Lanczos vector fed to A, ~1e-8 relative)."""
+    A^T A, up to the float32 application of A^T A (one pass of the solve kernel: dots and
+    sums in float32, about 1e-6 relative)."""
     s = rk_inputs.gaussian_system(2000, 100, seed=1)
     lmin, lmax, fro2 = oracle.spectrum(s.A)
     sp = rk.spectrum(_dev(s.A), k=100, seed=3)
     assert sp.steps == 100
-    assert sp.lambda_min == pytest.approx(lmin, rel=1e-6)
-    assert sp.lambda_max == pytest.approx(lmax, rel=1e-6)
+    assert sp.lambda_min == pytest.approx(lmin, rel=1e-5)
+    assert sp.lambda_max == pytest.approx(lmax, rel=1e-5)
     assert sp.fro2 == pytest.approx(fro2, rel=1e-12)
 
 
@@ -40,14 +41,14 @@ def test_spectrum_partial_inside_and_close(rk):
     lmin, lmax, fro2 = oracle.spectrum(s.A)
     sp = rk.spectrum(_dev(s.A), k=32, seed=0)
     assert sp.steps == 32
-    assert lmin * (1 - 1e-7) <= sp.lambda_min <= lmin * (1 + 5e-3)
-    assert lmax * (1 - 1e-4) <= sp.lambda_max <= lmax * (1 + 1e-7)
+    assert lmin * (1 - 1e-5) <= sp.lambda_min <= lmin * (1 + 5e-3)
+    assert lmax * (1 - 1e-4) <= sp.lambda_max <= lmax * (1 + 1e-5)
     # the weight of Eq. (best_alpha) from the estimate is within 1e-4 of the exact one
     for q in (8, 132):
         a_est = rk.alpha_star(q, sp.s_min, sp.s_max)
         a_ref = oracle.alpha_star(q, lmin / fro2, lmax / fro2)
         assert a_est == pytest.approx(a_ref, rel=1e-4)
-        assert a_est <= a_ref * (1 + 1e-7)   # s_min from above: the weight errs small
+        assert a_est <= a_ref * (1 + 1e-5)   # s_min from above: the weight errs small
 
 
 def test_spectrum_is_reproducible(rk):
@@ -90,3 +91,16 @@ def test_rka_optimal_weight_reaches_tolerance_faster(rk):
     assert i1.status == 0 and ia.status == 0
     assert ia.last_metric < 1e-6
     assert ia.rounds_done < i1.rounds_done / (0.4 * q)
+
+
+def test_spectrum_long_rows_two_pass(rk):
+    """Rows longer than the solve kernel holds (30000 columns) take the two residual
+    passes for A^T A v; the top of the spectrum still converges."""
+    s = rk_inputs.gaussian_system(800, 30000, seed=4)
+    A = _dev(s.A)
+    sp = rk.spectrum(A, k=40, seed=1)
+    # A A^T (800 x 800) has the same nonzero eigenvalues as A^T A
+    ev = np.linalg.eigvalsh(s.A.astype(np.float64) @ s.A.T.astype(np.float64))
+    assert sp.lambda_max == pytest.approx(ev[-1], rel=2e-3)
+    assert sp.lambda_max <= ev[-1] * (1 + 1e-9)   # a Ritz value, from below
+    assert sp.fro2 == pytest.approx(float(np.sum(s.A.astype(np.float64) ** 2)), rel=1e-12)

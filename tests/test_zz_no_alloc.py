@@ -87,12 +87,16 @@ def test_noalloc_stop_rule_reports_through_result(env):
 
 
 def test_noalloc_refuses_what_does_not_fit(env):
-    rk, _lib, L, plan, b, xs = env
-    x0 = torch.zeros(300, device="cuda")
-    x = torch.zeros(300, device="cuda")
+    rk, _lib, L, _, _, _ = env
+    import rk_inputs
+    A_t, b_t, _ = rk_inputs.gaussian_system_torch(600, 8000, seed=2, device="cuda")
+    big = rk.rk_setup(A_t)
+    x0 = torch.zeros(8000, device="cuda")
+    x = torch.zeros(8000, device="cuda")
     res = torch.zeros(24, dtype=torch.uint8, device="cuda")
-    # (q + 1) * 300 floats exceed 8 MiB for q >= 6990: refused before any device work
-    rc = _noalloc(L, plan, b, x0, x, 7000, 1, 1, 0, rk.make_opts(), res)
+    # 300 workers of 8000 columns: (300 + 1) * 8000 floats exceed 8 MiB: refused before
+    # any device work
+    rc = _noalloc(L, big, b_t, x0, x, 300, 2, 1, 0, rk.make_opts(), res)
     assert rc == _lib.RK_ETOOLARGE
     assert "fixed scratch" in L.rk_strerror(rc).decode()
     assert torch.count_nonzero(x) == 0 and torch.count_nonzero(res) == 0
