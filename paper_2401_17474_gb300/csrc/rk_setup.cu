@@ -113,21 +113,24 @@ __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int lane_mask) {
     return ((u128)hi << 64) | lo;
 }
 
+// One warp per row (warp-level reductions only): pass 1 finds max |a| as the
+// integer order of the absolute bit patterns, pass 2 forms the exact sum of the
+// scaled squares (integer, so its order does not matter; the row is then L1/L2
+// resident).  Non-finite rows set RK_EINVAL; zero rows get zero entries.
 template <class LD>
 __global__ void __launch_bounds__(256) row_weight_kernel(const uint8_t* __restrict__ A,
                                                          const float* __restrict__ row_scale,
                                                          int64_t m, int64_t n, int64_t lda_bytes,
                                                          SetupWs ws) {
-    __shared__ uint32_t s_max[8];
-    __shared__ u128 s_sum[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int64_t nchunks = (n + LD::kPerChunk - 1) / LD::kPerChunk;
-    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < m; i += (int64_t)gridDim.x * wpb) {
         const uint4* row = reinterpret_cast<const uint4*>(A + i * lda_bytes);
         const float sc = row_scale ? __ldg(row_scale + i) : 1.0f;
-        // pass 1: max |a| as the integer order of the absolute bit patterns
         uint32_t mx = 0;
-        for (int64_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
+#pragma unroll 4
+        for (int64_t c = lane; c < nchunks; c += 32) {
             float v[LD::kPerChunk];
             LD::decode(__ldg(row + c), sc, v);
 #pragma unroll
@@ -137,33 +140,19 @@ __global__ void __launch_bounds__(256) row_weight_kernel(const uint8_t* __restri
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) s_max[warp] = mx;
-        __syncthreads();
-        mx = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, s_max[w]);
-        if (mx >= 0x7F800000u) {  // inf or nan: no law; the row gets zero entries
-            if (threadIdx.x == 0) {
-                atomicCAS(&ws.info->status, 0, RK_EINVAL);
+        if (mx >= 0x7F800000u || mx == 0) {  // inf or nan: no law; zero row: weight 0
+            if (lane == 0) {
+                if (mx != 0) atomicCAS(&ws.info->status, 0, RK_EINVAL);
                 ws.R[i] = 0;
                 ws.e[i] = 0;
                 ws.inv[i] = 0.0f;
             }
-            __syncthreads();
-            continue;
-        }
-        if (mx == 0) {
-            if (threadIdx.x == 0) {
-                ws.R[i] = 0;
-                ws.e[i] = 0;
-                ws.inv[i] = 0.0f;
-            }
-            __syncthreads();
             continue;
         }
         const int e = frexp_exp_of_absbits(mx);
-        // pass 2: exact sum of the scaled squares (the row is now L1/L2 resident)
         u128 acc = 0;
-        for (int64_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
+#pragma unroll 4
+        for (int64_t c = lane; c < nchunks; c += 32) {
             float v[LD::kPerChunk];
             LD::decode(__ldg(row + c), sc, v);
 #pragma unroll
@@ -173,19 +162,14 @@ __global__ void __launch_bounds__(256) row_weight_kernel(const uint8_t* __restri
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) acc += shfl_xor_u128(acc, o);
-        if (lane == 0) s_sum[warp] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            u128 R = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) R += s_sum[w];
-            ws.R[i] = R;
+        if (lane == 0) {
+            ws.R[i] = acc;
             ws.e[i] = e;
-            const double rd = (double)(uint64_t)(R >> 64) * 18446744073709551616.0 + (double)(uint64_t)R;
+            const double rd = (double)(uint64_t)(acc >> 64) * 18446744073709551616.0 + (double)(uint64_t)acc;
             const double w2 = ldexp(rd, 2 * e - 102);
             ws.inv[i] = (float)(1.0 / w2);
-            atomicMax(&ws.info->H, bitlen128(R) + 2 * e - 102);
+            atomicMax(&ws.info->H, bitlen128(acc) + 2 * e - 102);
         }
-        __syncthreads();
     }
 }
 
@@ -441,7 +425,7 @@ int launch_setup(const void* A, rk_dtype dt, const float* row_scale, int64_t m, 
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int gw = (int)std::min<int64_t>(m, (int64_t)sms * 8);
+    const int gw = (int)std::min<int64_t>((m + 7) / 8, (int64_t)sms * 8);   // 8 rows (warps) a CTA
     const uint8_t* Ab = static_cast<const uint8_t*>(A);
     switch (dt) {
         case RK_F32:
