@@ -632,12 +632,14 @@ def run_precision(args, rk, dev):
         except Exception as e:
             out[f"{kind}_refine"] = {"error": str(e)}
         torch.cuda.empty_cache()
-    s3 = rk.Solver(plan, 152)
-    o3 = rk.make_opts(check_every=1, tol=args.tol, x_ref=xs,
-                      omega=rk.alpha_star(152, sp.s_min, sp.s_max))
-    t = _timed(lambda: s3.launch(b, x0, x, 1, 40000, args.seed, o3), reps=1)
-    out["fp32_rka_q152_alpha_star"] = {"ms": round(t, 2), "rounds": s3.info().rounds_done,
-                                       "metric": s3.info().last_metric}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    for qa in (sms, 32 * sms):
+        s3 = rk.Solver(plan, qa)
+        o3 = rk.make_opts(check_every=1, tol=args.tol, x_ref=xs,
+                          omega=rk.alpha_star(qa, sp.s_min, sp.s_max))
+        t = _timed(lambda: s3.launch(b, x0, x, 1, 40000, args.seed, o3), reps=1)
+        out[f"fp32_rka_q{qa}_alpha_star"] = {"ms": round(t, 2), "rounds": s3.info().rounds_done,
+                                             "metric": s3.info().last_metric}
     peak, kind = load_peaks()
     line = _base_line(args, METRIC, units / (total / 1e3), UNIT, total / args.steps,
                       {"workload": f"rkab_precision_{m}x{n}_q{q}_alpha{alpha}",
