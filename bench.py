@@ -577,6 +577,95 @@ def run_lsq(args, rk, dev):
     return line
 
 
+def _cgls_ls(A, b, iters=40, tol=1e-12, rows=32768):
+    """x_LS of min ||A x - b|| by conjugate gradients on the normal equations (CGLS) in
+    FP64, A (float32, on the device) promoted in row chunks: the measurement's reference
+    solution (Section 3.1 names CGLS for x_LS), not part of the solver."""
+    import torch
+    m, n = A.shape
+
+    def av(v):
+        out = torch.empty(m, dtype=torch.float64, device=A.device)
+        for r0 in range(0, m, rows):
+            out[r0:r0 + rows] = A[r0:r0 + rows].double() @ v
+        return out
+
+    def atv(y):
+        acc = torch.zeros(n, dtype=torch.float64, device=A.device)
+        for r0 in range(0, m, rows):
+            acc += A[r0:r0 + rows].double().T @ y[r0:r0 + rows]
+        return acc
+
+    x = torch.zeros(n, dtype=torch.float64, device=A.device)
+    r = b.double().clone()
+    s_ = atv(r)
+    p = s_.clone()
+    gamma = float(s_ @ s_)
+    g0 = gamma
+    for _ in range(iters):
+        if gamma <= tol * tol * g0:
+            break
+        qv = av(p)
+        a = gamma / float(qv @ qv)
+        x += a * p
+        r -= a * qv
+        s_ = atv(r)
+        gn = float(s_ @ s_)
+        p = s_ + (gn / gamma) * p
+        gamma = gn
+    return x
+
+
+def precision_inconsistent(rk, A, plan, b, n, q, alpha, args, dev):
+    """The inconsistent variant: b + e, e ~ N(0, 1e-4^2); time to ||x - x_LS||/||x_LS|| < 1e-6
+    for plain FP32 RKAB, BF16 / FP8 + refinement and RKA with alpha* (4864 workers), x_LS from
+    FP64 CGLS.  A run that stops at its convergence horizon above 1e-6 reports its last error."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(args.seed) * 1000003 + 3)
+    b_inc = (b.double() + 1e-4 * torch.randn(b.numel(), dtype=torch.float64, device=dev,
+                                              generator=g)).float()
+    t0 = time.perf_counter()
+    x_ls = _cgls_ls(A, b_inc)
+    t_cgls = time.perf_counter() - t0
+    xr = x_ls.float()
+    x0 = torch.zeros(n, dtype=torch.float32, device=dev)
+    x = torch.empty_like(x0)
+    out = {"noise": 1e-4, "x_ls_reference": f"FP64 CGLS ({t_cgls:.1f} s)"}
+    s = rk.Solver(plan, q)
+    o = rk.make_opts(check_every=1, tol=args.tol, x_ref=xr)
+    t = _timed(lambda: s.launch(b_inc, x0, x, alpha, args.max_rounds, args.seed, o), reps=1)
+    out["fp32_plain"] = {"ms": round(t, 2), "rounds": s.info().rounds_done,
+                         "metric": s.info().last_metric}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sp = rk.spectrum(A, k=4)
+    qa = 32 * sms
+    sa = rk.Solver(plan, qa)
+    oa = rk.make_opts(check_every=1, tol=args.tol, x_ref=xr,
+                      omega=rk.alpha_star(qa, sp.s_min, sp.s_max))
+    t = _timed(lambda: sa.launch(b_inc, x0, x, 1, 20000, args.seed, oa), reps=1)
+    out[f"fp32_rka_q{qa}_alpha_star"] = {"ms": round(t, 2), "rounds": sa.info().rounds_done,
+                                         "metric": sa.info().last_metric}
+    for kind in ("bf16", "fp8"):
+        try:
+            Aq, sc = rk.quantize(A, kind)
+            lowp = rk.rk_setup(Aq, kind, sc)
+            ref = rk.Refiner(lowp, q)
+            oo = rk.make_opts(check_every=0, tol=args.tol, x_ref=xr)
+            holder = {}
+
+            def go():
+                holder["i"] = ref.run(A, b_inc, x0, x, alpha, 4, 40, args.seed, oo)
+            t = _timed(go, reps=1)
+            out[f"{kind}_refine"] = {"ms": round(t, 2), "outer": holder["i"].outer_done,
+                                     "inner_rounds": 4, "metric": holder["i"].last_metric}
+            del Aq, lowp, ref
+        except Exception as e:
+            out[f"{kind}_refine"] = {"error": str(e)}
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_precision(args, rk, dev):
     """1e6 x 16000 consistent system: plain FP32 RKAB (q = 132, alpha = n) against BF16 and
     FP8 e4m3 stored rows with refinement on the FP32 master, time to ||x - x*||/||x*|| < 1e-6;
@@ -640,6 +729,7 @@ def run_precision(args, rk, dev):
         t = _timed(lambda: s3.launch(b, x0, x, 1, 40000, args.seed, o3), reps=1)
         out[f"fp32_rka_q{qa}_alpha_star"] = {"ms": round(t, 2), "rounds": s3.info().rounds_done,
                                              "metric": s3.info().last_metric}
+    out["inconsistent"] = precision_inconsistent(rk, A, plan, b, n, q, alpha, args, dev)
     peak, kind = load_peaks()
     line = _base_line(args, METRIC, units / (total / 1e3), UNIT, total / args.steps,
                       {"workload": f"rkab_precision_{m}x{n}_q{q}_alpha{alpha}",
