@@ -341,6 +341,36 @@ int rk_residual(const float *A, int64_t m, int64_t n, int64_t lda, const float *
                 size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Solve with a stopping rule that needs no reference solution (the          */
+/* convergence checks of Section 3.1 on the residual r = b - A x):           */
+/*   RK_CRIT_RESIDUAL  ||r|| / ||b||                  (consistent systems)    */
+/*   RK_CRIT_NORMAL    ||A^T r|| / (||A||_F ||r||)    (least squares,         */
+/*                     Eq. (ls_system); one more pass over A per check)       */
+/* every check_every rounds, with the float64-class residual of rk_residual  */
+/* on the float32 rows.                                                       */
+/* ------------------------------------------------------------------------ */
+typedef enum { RK_CRIT_RESIDUAL = 2, RK_CRIT_NORMAL = 3 } rk_residual_criterion;
+
+/* Bytes of device workspace rkab_solve_residual needs. */
+size_t rk_solve_residual_workspace_bytes(const rk_plan *plan, int q);
+
+/* Rounds of rkab_solve (opts as there; its criterion, tol and check_every are not used)
+ * in stretches of check_every rounds that continue one stream of draws (round0 advances),
+ * each followed by the residual criterion; stops after the first check with
+ * metric < tol, or after max_rounds.
+ *   A32      device float32 rows of the same system (m x n, lda32); NULL uses the plan's
+ *            rows (float32 plans only)
+ *   x        device, n floats (may alias x0); the iterate after the last stretch
+ * Synchronous (waits for `stream` after every stretch).  *rounds_done and *last_metric
+ * (host, may be NULL) receive the rounds run and the last criterion value; returns RK_OK,
+ * or the first error (device status of a stretch included). */
+int rkab_solve_residual(const rk_plan *plan, const float *A32, int64_t lda32, const float *b,
+                        const float *x0, float *x, int q, int64_t alpha, int64_t max_rounds,
+                        int64_t check_every, uint64_t seed, const rk_opts *opts, int criterion,
+                        double tol, void *workspace, size_t ws_bytes, void *stream,
+                        int64_t *rounds_done, double *last_metric);
+
+/* ------------------------------------------------------------------------ */
 /* Optimal uniform weight of RKA (Section 2.3.1, Eq. (best_alpha)) for a      */
 /* consistent system, from s_min = sigma_min^2 / ||A||_F^2 and               */
 /* s_max = sigma_max^2 / ||A||_F^2:                                          */

@@ -29,6 +29,7 @@ from .api import (  # noqa: F401
     rkab_refine,
     rkab_lstsq,
     rkab_solve,
+    rkab_solve_residual,
     spectrum,
     transpose,
 )

@@ -94,6 +94,13 @@ _SIG = {
     "rk_residual_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     "rk_residual": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _V, _V,
                                    _V, _V, ctypes.c_int, _V, ctypes.c_size_t, _V]),
+    "rk_solve_residual_workspace_bytes": (ctypes.c_size_t, [_V, ctypes.c_int]),
+    "rkab_solve_residual": (ctypes.c_int, [_V, _V, ctypes.c_int64, _V, _V, _V, ctypes.c_int,
+                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_uint64, ctypes.POINTER(RkOpts), ctypes.c_int,
+                                           ctypes.c_double, _V, ctypes.c_size_t, _V,
+                                           ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_double)]),
     "rk_alpha_star": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "rk_spectrum_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int]),
     "rk_spectrum": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,

@@ -230,6 +230,34 @@ def rkab_solve(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, rounds: int =
     return x, info
 
 
+CRITERIA = {"residual": 2, "normal": 3}
+
+
+def rkab_solve_residual(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, max_rounds: int = 100,
+                        check_every: int = 1, tol: float = 1e-6, criterion="normal", seed: int = 0,
+                        A32=None, stream=None, **opt_kw):
+    """RKAB stopped by a residual criterion ('residual': ||r||/||b||; 'normal':
+    ||A^T r||/(||A||_F ||r||)) checked every check_every rounds; returns (x, rounds, metric).
+    A32: float32 rows of the system when the plan stores BF16/FP8 rows."""
+    b = _vec(b, plan.m, "b")
+    if x0 is None:
+        x0 = torch.zeros(plan.n, dtype=torch.float32, device=plan.device)
+    x0 = _vec(x0, plan.n, "x0")
+    x = torch.empty(plan.n, dtype=torch.float32, device=plan.device)
+    lib = _lib.load()
+    ws = _workspace(lib.rk_solve_residual_workspace_bytes(plan.handle, q), plan.device)
+    opts = make_opts(**opt_kw)
+    done = ctypes.c_int64(0)
+    metric = ctypes.c_double(-1.0)
+    crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
+    check(lib.rkab_solve_residual(plan.handle, _ptr(A32), 0 if A32 is None else A32.stride(0),
+                                  _ptr(b), _ptr(x0), _ptr(x), q, alpha, max_rounds, check_every,
+                                  seed, ctypes.byref(opts), crit, float(tol), _ptr(ws), ws.numel(),
+                                  _stream(stream), ctypes.byref(done), ctypes.byref(metric)),
+          "rkab_solve_residual")
+    return x, int(done.value), float(metric.value)
+
+
 def rka_solve(plan: Plan, b, x0=None, q: int = 1, rounds: int = 1, seed: int = 0, **kw):
     """RKA (alpha = 1): Eq. (rka_uni_weights)."""
     return rkab_solve(plan, b, x0, q=q, alpha=1, rounds=rounds, seed=seed, **kw)

@@ -352,6 +352,112 @@ int rkab_adjoint(const rk_plan* plan_A, const rk_plan* plan_At, const float* b, 
                        grad_b, grad_A, ldg, g, workspace, static_cast<cudaStream_t>(stream));
 }
 
+size_t rk_solve_residual_workspace_bytes(const rk_plan* plan, int q) {
+    if (!plan || q < 1) return 0;
+    return align256(solve_ws_bytes(&plan->p, q)) + align256(residual_ws_bytes(plan->p.m, plan->p.n)) +
+           256;
+}
+
+int rkab_solve_residual(const rk_plan* plan, const float* A32, int64_t lda32, const float* b,
+                        const float* x0, float* x, int q, int64_t alpha, int64_t max_rounds,
+                        int64_t check_every, uint64_t seed, const rk_opts* opts, int criterion,
+                        double tol, void* workspace, size_t ws_bytes, void* stream,
+                        int64_t* rounds_done, double* last_metric) {
+    if (rounds_done) *rounds_done = 0;
+    if (last_metric) *last_metric = -1.0;
+    if (!plan || !b || !x0 || !x || !workspace || q < 1 || alpha < 1 || max_rounds < 0 ||
+        check_every < 1 || !(tol >= 0.0) || (criterion != RK_CRIT_RESIDUAL && criterion != RK_CRIT_NORMAL))
+        return RK_EINVAL;
+    const Plan& pl = plan->p;
+    if (!A32) {
+        if (pl.dt != RK_F32) return RK_EINVAL;
+        A32 = static_cast<const float*>(pl.A);
+        lda32 = pl.lda;
+    }
+    if (lda32 < pl.n) return RK_EINVAL;
+    if (!aligned16(A32) || (lda32 * 4) % 16 != 0 || ((uintptr_t)workspace & 255u) != 0) return RK_EALIGN;
+    rk_opts o;
+    rk_opts_default(&o);
+    if (opts) o = *opts;
+    o.criterion = 0;
+    o.check_every = 0;
+    o.x_ref = nullptr;
+    if (!valid_opts(o, q)) return RK_EINVAL;
+    if (ws_bytes < rk_solve_residual_workspace_bytes(plan, q)) return RK_EWORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint8_t* p = static_cast<uint8_t*>(workspace);
+    SolveInfo* info = reinterpret_cast<SolveInfo*>(p);
+    float* V = reinterpret_cast<float*>(p + align256(sizeof(SolveInfo)));
+    p += align256(solve_ws_bytes(&pl, q));
+    void* rws = p;
+    p += align256(residual_ws_bytes(pl.m, pl.n));
+    double* norms = reinterpret_cast<double*>(p);
+    // ||A||_F^2 = T 2^L from the plan's integer weights (relative truncation below m / T)
+    double fro = 0.0;
+    if (criterion == RK_CRIT_NORMAL) {
+        uint64_t T = 0;
+        int32_t L = 0;
+        const int rc = rk_plan_status(plan, stream, &T, &L);
+        if (rc != RK_OK) return rc;
+        fro = std::sqrt(std::ldexp((double)T, L));
+    }
+    // ||b|| for the relative residual: the residual of x = 0
+    double bnorm = 1.0;
+    if (criterion == RK_CRIT_RESIDUAL) {
+        if (cudaMemsetAsync(x, 0, (size_t)pl.n * 4, st) != cudaSuccess) return RK_ECUDA;
+        int rc = launch_residual(A32, pl.m, pl.n, lda32, b, x, nullptr, norms, 0, rws, st);
+        double h[2];
+        if (rc != RK_OK) return rc;
+        if (cudaMemcpyAsync(h, norms, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return RK_ECUDA;
+        bnorm = h[0] > 0.0 ? h[0] : 1.0;
+    }
+    const float* start = x0;
+    int64_t done = 0;
+    while (done < max_rounds) {
+        const int64_t k = (max_rounds - done) < check_every ? (max_rounds - done) : check_every;
+        SolveArgs a;
+        a.plan = &pl;
+        a.b = b;
+        a.x0 = start;
+        a.x = x;
+        a.q = q;
+        a.alpha = alpha;
+        a.rounds = k;
+        a.seed = seed;
+        a.opts = o;
+        a.opts.round0 = o.round0 + done;
+        a.info = info;
+        a.ldv = (pl.n + 3) / 4 * 4;
+        a.V = V;
+        if (cudaMemsetAsync(info, 0, sizeof(SolveInfo), st) != cudaSuccess) return RK_ECUDA;
+        int rc = launch_solve(a, st);
+        if (rc != RK_OK) return rc;
+        start = x;
+        rc = launch_residual(A32, pl.m, pl.n, lda32, b, x, nullptr, norms, criterion == RK_CRIT_NORMAL,
+                             rws, st);
+        if (rc != RK_OK) return rc;
+        double h[2];
+        int status = 0;
+        if (cudaMemcpyAsync(h, norms, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&status, &info->status, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return RK_ECUDA;
+        if (status != 0) return status;
+        done += k;
+        if (rounds_done) *rounds_done = done;
+        double metric;
+        if (criterion == RK_CRIT_RESIDUAL) metric = h[0] / bnorm;
+        else metric = (h[0] > 0.0 && fro > 0.0) ? h[1] / (fro * h[0]) : 0.0;
+        if (last_metric) *last_metric = metric;
+        if (!std::isfinite(metric)) return RK_EDIVERGED;
+        if (metric < tol) break;
+    }
+    return RK_OK;
+}
+
 double rk_alpha_star(int q, double s_min, double s_max) {
     if (q < 1 || !(s_min >= 0.0 && s_min <= 1.0) || !(s_max >= 0.0 && s_max <= 1.0)) return 0.0;
     if (q == 1 || s_max - s_min <= 1.0 / (double)(q - 1)) return (double)q / (1.0 + (q - 1) * s_min);

@@ -416,12 +416,17 @@ static int grid_for(int64_t m, int threads) {
     return (int)(g < 1 ? 1 : g);
 }
 
-int launch_setup(const void* A, rk_dtype dt, const float* row_scale, int64_t m, int64_t n,
-                 int64_t lda, const SetupWs& ws, cudaStream_t st) {
-    cudaMemsetAsync(ws.info, 0, sizeof(SetupInfo), st);
+__global__ void setup_info_init_kernel(SetupInfo* info) {
     SetupInfo init{};
     init.H = kNoRows;
-    cudaMemcpyAsync(ws.info, &init, sizeof(SetupInfo), cudaMemcpyHostToDevice, st);
+    *info = init;
+}
+
+int launch_setup(const void* A, rk_dtype dt, const float* row_scale, int64_t m, int64_t n,
+                 int64_t lda, const SetupWs& ws, cudaStream_t st) {
+    // the header is reset on the device (no host copy: the call stays capturable)
+    setup_info_init_kernel<<<1, 1, 0, st>>>(ws.info);
+    count_launch();
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

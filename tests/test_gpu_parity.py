@@ -373,3 +373,34 @@ def test_zero_weight_block_is_refused(rk):
     assert e.value.code == -1
     with pytest.raises(rk.RkError):
         rk.rkab_solve(plan, _dev(s.b), q=4, alpha=10, rounds=1, sampling="blocks", same_stream=True)
+
+
+def test_residual_stopping_rules(rk):
+    """Stopping rules on the residual (no reference solution): the stretches of rounds
+    continue one stream of draws (x equals the oracle's uninterrupted run), and the
+    reported criterion equals the FP64 value at the returned x."""
+    s = rk_inputs.gaussian_system(2000, 100, seed=0)
+    tab = oracle.table(s.A)
+    plan = rk.rk_setup(_padded(s.A, rk))
+    b64 = s.b.astype(np.float64)
+    x, rounds, metric = rk.rkab_solve_residual(plan, _dev(s.b), q=4, alpha=100, max_rounds=400,
+                                               check_every=3, tol=1e-6, criterion="residual",
+                                               seed=2)
+    assert 0 < rounds < 400 and rounds % 3 == 0 and 0 <= metric < 1e-6
+    x_o = oracle.rkab(s.A, b64, np.zeros(100), q=4, alpha=100, rounds=rounds, seed=2, tab=tab)
+    assert _rel(x.cpu().numpy(), x_o) < TOL
+    _, rn, _ = oracle.residual(s.A, b64, x.cpu().numpy().astype(np.float64))
+    assert metric == pytest.approx(rn / np.linalg.norm(b64), rel=1e-6)
+    # least squares: ||A^T r|| / (||A||_F ||r||) on an inconsistent system, uneven stretches
+    si = rk_inputs.gaussian_system(2000, 100, seed=1, noise=0.1)
+    tabi = oracle.table(si.A)
+    plani = rk.rk_setup(_padded(si.A, rk))
+    bi = si.b.astype(np.float64)
+    x, rounds, metric = rk.rkab_solve_residual(plani, _dev(si.b), q=3, alpha=50, max_rounds=30,
+                                               check_every=7, tol=0.0, criterion="normal", seed=4)
+    assert rounds == 30
+    x_o = oracle.rkab(si.A, bi, np.zeros(100), q=3, alpha=50, rounds=30, seed=4, tab=tabi)
+    assert _rel(x.cpu().numpy(), x_o) < TOL
+    _, rn, an = oracle.residual(si.A, bi, x.cpu().numpy().astype(np.float64))
+    fro = np.sqrt(np.sum(si.A.astype(np.float64) ** 2))
+    assert metric == pytest.approx(an / (fro * rn), rel=1e-5)
