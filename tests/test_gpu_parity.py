@@ -404,3 +404,27 @@ def test_residual_stopping_rules(rk):
     _, rn, an = oracle.residual(si.A, bi, x.cpu().numpy().astype(np.float64))
     fro = np.sqrt(np.sum(si.A.astype(np.float64) ** 2))
     assert metric == pytest.approx(an / (fro * rn), rel=1e-5)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (3, 1), (5, 2), (7, 5), (2, 9)])
+@pytest.mark.parametrize("q,alpha", [(1, 1), (3, 7)])
+def test_degenerate_shapes_match_oracle(rk, m, n, q, alpha):
+    """Single rows and columns, fewer rows than workers, wide systems: the same draws and
+    x within 1e-4 of the oracle (the row padding and the tail masking at their limits)."""
+    rng = np.random.default_rng(m * 31 + n)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    b = rng.standard_normal(m).astype(np.float32)
+    tab = oracle.table(A)
+    plan = rk.rk_setup(_padded(A, rk))
+    x, info = rk.rkab_solve(plan, _dev(b), q=q, alpha=alpha, rounds=5, seed=8, check_every=0)
+    assert info.status == 0
+    x_o = oracle.rkab(A, b.astype(np.float64), np.zeros(n), q=q, alpha=alpha, rounds=5, seed=8,
+                      tab=tab)
+    assert _rel(x.cpu().numpy(), x_o) < TOL
+
+
+def test_empty_system_is_refused(rk):
+    with pytest.raises((rk.RkError, ValueError)):
+        rk.rk_setup(torch.zeros((0, 4), dtype=torch.float32, device="cuda"))
+    with pytest.raises((rk.RkError, ValueError)):
+        rk.rk_setup(torch.zeros((4, 0), dtype=torch.float32, device="cuda"))
