@@ -173,11 +173,13 @@ int rk_sample_indices_ex(const rk_plan *plan, uint64_t seed, uint32_t worker, ui
 /* round from v = x, applies `alpha` projections                            */
 /*   v <- v + omega (b_i - <A_i, v>) / ||A_i||^2 A_i^T      (Eq. (alg))      */
 /* with rows i drawn from Eq. (prob_line), and the round ends with          */
-/*   x <- (1/q) sum_{gamma = 0}^{q-1} v_gamma      (summed in that order).   */
+/*   x <- (1/q) sum_{gamma = 0}^{q-1} v_gamma   (a fixed order, every run).   */
 /* alpha = 1 is RKA, Eq. (rka_uni_weights); q = 1 is RK.                     */
 /* One persistent kernel runs all rounds: every worker is one CTA (or a      */
 /* cluster of CTAs splitting x) that keeps its v on chip and streams the     */
-/* sampled rows from HBM into a ring of shared-memory stages.               */
+/* sampled rows from HBM into a ring of shared-memory stages; RKA with more  */
+/* workers than SMs gives each CTA a share of the workers, whose single      */
+/* projections from x it sums (the same result, Eq. (rka_eq)).               */
 /* ------------------------------------------------------------------------ */
 
 /* Bytes of device workspace one solve with q workers needs: with r = min(q, twice the SM
