@@ -84,3 +84,29 @@ def test_alpha_star_is_the_oracle_formula(lib):
     assert L.rk_spectrum_workspace_bytes(1000, 100, 32) > 33 * 100 * 8
     assert L.rk_spectrum_workspace_bytes(1000, 100, 0) == 0
     assert L.rk_spectrum_workspace_bytes(1000, 100, 513) == 0
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary header compiles as C99 and C++ (no torch or CUDA types), and a C
+    caller links against the library's exported symbols."""
+    src = tmp_path / "caller.c"
+    src.write_text('#include "rkab.h"\n'
+                   'int main(void) {\n'
+                   '    rk_opts o; rk_opts_default(&o);\n'
+                   '    return (int)(rk_setup_workspace_bytes(10, 4) == 0) + (o.omega != 1.0f)\n'
+                   '           + (rk_alpha_star(1, 0.1, 0.2) != 1.0);\n'
+                   '}\n')
+    inc = os.path.join(ROOT, "include")
+    for cc, std in (("gcc", "-std=c99"), ("g++", "-std=c++17")):
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-I", inc, "-fsyntax-only",
+                            "-x", "c" if cc == "gcc" else "c++", str(src)],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    from paper_2401_17474_gb300 import build
+    lib = build.build()
+    exe = tmp_path / "caller"
+    r = subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), lib, "-o", str(exe),
+                        "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
