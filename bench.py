@@ -229,7 +229,14 @@ def sample_alpha(A_np, b_np, tab, q, seed, threads, target_s):
 
 
 def cpu_model():
-    """The host CPU's model name (Linux /proc/cpuinfo; 'unknown' elsewhere)."""
+    """The host CPU's model name (lscpu, else /proc/cpuinfo; 'unknown' elsewhere)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
