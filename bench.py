@@ -866,11 +866,12 @@ def run_ours(args):
     import torch
 
     ws, rank, local = dist_env()
+    torch.cuda.set_device(local)   # before the process group: NCCL binds the current device
+    dev = torch.device("cuda", local)
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
+                                device_id=dev if torch.cuda.is_available() else None)
 
     import rk_inputs
     import paper_2401_17474_gb300 as rk
