@@ -13,8 +13,8 @@ value = row projections per second over all timed steps (q * alpha * rounds
 per step); ms_per_step = time to tolerance including the setup.
 
 --impl reference times the FP64 CPU oracle on this machine's host cores on a
-bounded sample of the same workload (the reference arm of this build: the
-paper's own implementation is CPU code that is not available here).
+bounded sample of the same workload (the paper's own implementation is CPU code
+that is not available, so the oracle serves as the reference).
 
 Multi-GPU: the path is run as independent replicas (one per rank, no
 collective in the data path); value sums the replicas' projections over the

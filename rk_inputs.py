@@ -7,7 +7,7 @@ averages), only random draws and the construction of the right-hand side.
 The shapes and value distributions follow the workloads of the paper
 (Section 3.1: dense overdetermined systems, consistent ``b = A x*`` and an
 inconsistent variant ``b + xi`` with Gaussian noise) at the sizes of the
-benchmark configurations; entries are iid N(0, 1) unless a row-scale spread
+benchmark workloads; entries are iid N(0, 1) unless a row-scale spread
 is asked for (rows multiplied by ``10**U(-d, d)``).
 
 Each quantity draws from its own stream so that changing one shape does not
