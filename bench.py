@@ -194,12 +194,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes(n, q, alpha, rounds, elem=4):
+def algorithmic_bytes(n, q, alpha, rounds, elem=4, sms=None):
     """Bytes the method must move: per projection the row (n*elem), b_i, 1/||A_i||^2
     and the alias entry (thr64 + alias); per round the averaging traffic (write V,
-    read V, reload x in every CTA) ~ 3 q n 4."""
+    read V, reload x in every CTA) ~ 3 r n 4 for the r partial iterates written.  r = q,
+    except for RKA (alpha = 1) with more workers than SMs, where each of the sms CTAs
+    sums its workers' projections into one partial iterate (r = sms)."""
     per_proj = n * elem + 4 + 4 + 12
-    return rounds * (q * alpha * per_proj + 3 * q * n * 4)
+    r = sms if (alpha == 1 and sms is not None and q > sms) else q
+    return rounds * (q * alpha * per_proj + 3 * r * n * 4)
 
 
 # ---------------------------------------------------------------------------
@@ -993,7 +996,8 @@ def run_ours(args):
     # roofline of the dominant kernel (the persistent solve), from its own events
     peak, peak_kind = load_peaks()
     kmean_s = sum(kern_ms) / len(kern_ms) / 1e3
-    alg = algorithmic_bytes(n, q, alpha, rounds_t, elem)
+    alg = algorithmic_bytes(n, q, alpha, rounds_t, elem,
+                            torch.cuda.get_device_properties(dev).multi_processor_count)
     achieved = alg / kmean_s / 1e9
     default_cfg = ((m, n, q, alpha, args.dtype, args.cluster, omega) ==
                    (80000, 10000, 132, 10000, "f32", 0, 1.0))
