@@ -69,13 +69,14 @@ def parse():
                     help="relaxation of the timed solve: a number, or 'star' for alpha* of "
                          "Eq. (best_alpha) from the GPU spectrum estimate (computed before timing)")
     ap.add_argument("--workload", default="consistent",
-                    choices=["consistent", "lsq", "precision", "horizon", "adjoint"],
+                    choices=["consistent", "lsq", "precision", "horizon", "adjoint", "setup"],
                     help="consistent: 80000 x 10000 to 1e-6 (default); lsq: 200000 x 20000 "
                          "row-scaled inconsistent system, budget of rounds with the normal-equation "
                          "criterion logged every round; precision: 1e6 x 16000, FP32 vs BF16/FP8 "
                          "+ refinement to 1e-6; horizon: 80000 x 1000 inconsistent system, error "
                          "to x_LS and residual along RKA / RKAB runs for several worker counts; "
-                         "adjoint: backward pass of the least-squares solve at 200000 x 20000")
+                         "adjoint: backward pass of the least-squares solve at 200000 x 20000; "
+                         "setup: rk_setup alone on --m x --n stored as --dtype")
     return ap.parse_args()
 
 
@@ -811,6 +812,63 @@ def run_horizon(args, rk, dev):
     return line
 
 
+def run_setup(args, rk, dev):
+    """Row a1 alone: rk_setup (exact row weights, prefix sums, alias table, 1/||A_i||^2) of
+    an m x n Gaussian matrix (default 80000 x 10000) stored as --dtype, timed over --steps
+    setups after --warmup.  One step = one setup; A (3.2 GB FP32) is larger than L2."""
+    import torch
+
+    import rk_inputs
+    m, n = args.m, args.n
+    A, _, _ = rk_inputs.gaussian_system_torch(m, n, seed=args.seed, device=str(dev))
+    scale = None
+    if args.dtype != "f32":
+        A, scale = rk.quantize(A, args.dtype)
+    elem = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
+    ws_bytes = rk.api._lib.load().rk_setup_workspace_bytes(m, n)
+    work = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def setup():
+        if args.dtype == "f32":
+            return rk.rk_setup(A, stream=stream, workspace=work)
+        return rk.rk_setup(A, args.dtype, scale, stream=stream, workspace=work)
+
+    for _ in range(max(args.warmup, 3)):
+        plan = setup()
+    plan.status()
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0")
+    launches0 = rk.launch_count()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan = setup()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    launches = rk.launch_count() - launches0
+    T, L = plan.status()
+    ms = e0.elapsed_time(e1) / args.steps
+    a_bytes = m * n * elem
+    # one read of A (+ the row scales of FP8 rows); the tables: R (16 B), e, K, P, thr64,
+    # alias, 1/||A_i||^2 and the split/compaction arrays, about 80 B a row written or read
+    alg = a_bytes + (4 * m if args.dtype == "fp8" else 0) + 80 * m
+    peak, kind = load_peaks()
+    line = _base_line(args, "rk_setup_throughput", a_bytes / (ms / 1e3) / 1e9, "GB/s of A", ms,
+                      {"workload": f"rk_setup_{m}x{n}_{args.dtype}", "m": m, "n": n,
+                       "T": T, "L": L,
+                       "l2": "inputs larger than L2 (A is %.1f GB)" % (a_bytes / 1e9)},
+                      clk, launches)
+    line["dtype"] = args.dtype
+    line["roofline"] = {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak,
+                        "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None,
+                        "peak_kind": kind, "kernel": "rk_setup (all its kernels, one step)",
+                        "algorithmic_bytes": alg}
+    return line
+
+
 def run_adjoint_large(args, rk, dev):
     """Differentiation form at 200000 x 20000 (b = A x* + N(0, 1e-3^2), L = 0.5||x - x_t||^2):
     forward RKA with alpha* (4864 workers), then the backward pass -- A^T copy and its
@@ -884,7 +942,7 @@ def run_ours(args):
     if args.workload != "consistent":
         if rank == 0:
             fn = {"lsq": run_lsq, "precision": run_precision, "horizon": run_horizon,
-                  "adjoint": run_adjoint_large}[args.workload]
+                  "adjoint": run_adjoint_large, "setup": run_setup}[args.workload]
             print(json.dumps(fn(args, rk, dev)), flush=True)
         if ws > 1:
             import torch.distributed as dist

@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <cstdio>
 
+#include "rk_common.cuh"
 #include "rk_internal.h"
 
 namespace rk {
@@ -27,6 +28,11 @@ struct LoadF32 {
         out[2] = __uint_as_float(c.z);
         out[3] = __uint_as_float(c.w);
     }
+    // float32 bits of the largest |decoded value| of the chunk
+    __device__ static uint32_t max_abs_bits(const uint4& c, float s) {
+        (void)s;
+        return max(max(c.x & 0x7FFFFFFFu, c.y & 0x7FFFFFFFu), max(c.z & 0x7FFFFFFFu, c.w & 0x7FFFFFFFu));
+    }
 };
 
 struct LoadBF16 {
@@ -40,6 +46,12 @@ struct LoadBF16 {
             out[2 * k] = __uint_as_float(w[k] << 16);
             out[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
         }
+    }
+    __device__ static uint32_t max_abs_bits(const uint4& c, float s) {
+        (void)s;
+        const uint32_t h = __vmaxu2(__vmaxu2(c.x & 0x7FFF7FFFu, c.y & 0x7FFF7FFFu),
+                                    __vmaxu2(c.z & 0x7FFF7FFFu, c.w & 0x7FFF7FFFu));
+        return max(h & 0xFFFFu, h >> 16) << 16;
     }
 };
 
@@ -68,12 +80,20 @@ struct LoadFP8 {
             for (int b = 0; b < 4; ++b) out[4 * k + b] = __fmul_rn(s, e4m3_to_float((w[k] >> (8 * b)) & 0xFFu));
         }
     }
+    // e4m3 decoding is increasing in the 7-bit magnitude code and rounding is
+    // monotone and sign-symmetric, so the largest |s q| is |s| times the
+    // largest magnitude code's value
+    __device__ static uint32_t max_abs_bits(const uint4& c, float s) {
+        const uint32_t b = __vmaxu4(__vmaxu4(c.x & 0x7F7F7F7Fu, c.y & 0x7F7F7F7Fu),
+                                    __vmaxu4(c.z & 0x7F7F7F7Fu, c.w & 0x7F7F7F7Fu));
+        const uint32_t code = max(max(b & 0xFFu, (b >> 8) & 0xFFu), max((b >> 16) & 0xFFu, b >> 24));
+        return __float_as_uint(__fmul_rn(s, e4m3_to_float(code))) & 0x7FFFFFFFu;
+    }
 };
 
 // ---------------------------------------------------------------------------
 // Row weights: R_i = sum_j floor(a_ij^2 2^(102 - 2 e_i)) exactly, e_i the
-// frexp exponent of max_j |a_ij|; h_i = bitlength(R_i) + 2 e_i - 102 (max -> H);
-// inv_i = 1 / ||A_i||^2 in float32.
+// frexp exponent of max_j |a_ij|; h_i = bitlength(R_i) + 2 e_i - 102 (max -> H).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int frexp_exp_of_absbits(uint32_t ab) {
     const uint32_t E = ab >> 23;
@@ -81,24 +101,65 @@ __device__ __forceinline__ int frexp_exp_of_absbits(uint32_t ab) {
     return (32 - __clz(ab)) - 149;  // subnormal: M 2^-149 with M in [2^(bl-1), 2^bl)
 }
 
-// floor(a^2 2^(102 - 2 e)) for |a| < 2^e, as an exact 128-bit integer.
-__device__ __forceinline__ u128 scaled_square(uint32_t ab, int e) {
-    const uint32_t E = ab >> 23;
-    uint64_t mant;
-    int ex;
-    if (E != 0) {
-        mant = (ab & 0x7FFFFFu) | 0x800000u;
-        ex = (int)E - 150;
-    } else {
-        mant = ab;
-        ex = -149;
-    }
-    const uint64_t sq = mant * mant;  // < 2^48, exact
-    const int s = 2 * ex + 102 - 2 * e;
-    if (s >= 0) return ((u128)sq) << s;
-    if (s <= -64) return 0;
-    return (u128)(sq >> (-s));
+// Exact sum of floor(a^2 2^(102 - 2 e)) over entries with |a| < 2^e.  For an
+// entry mant 2^(E - 150) (E = 1 for a subnormal, without the implicit bit),
+// U = |a| 2^(51 - e) = mant 2^k with k = E - 99 - e.  When k >= 0, U is an
+// integer below 2^51 and the term is U^2 = Uh^2 2^54 + Uh Ul 2^28 + Ul^2 with
+// U = Uh 2^27 + Ul, so three 32 x 32 -> 64-bit multiply-adds take it exactly
+// (each sum below 2^63 for up to 512 entries).  When k < 0 the term is
+// floor(mant^2 2^(2k)).
+//
+// SqAcc is for rows with e >= -90, where k <= 27 and every zero or subnormal
+// entry has k < 0: add() takes the k >= 0 terms with 32-bit funnel shifts
+// (Uh = mant >> (27 - k), Ul = (mant << k) mod 2^27; both clamp to 0 when
+// k < 0) and tracks the smallest nonzero |a|; when that lies below 2^(kbase-127)
+// (some entry has k < 0) add_small() adds the k < 0 terms.  SqAccWide takes
+// any row.
+// acc += a * b (32 x 32 -> 64 bits) as one multiply-add
+__device__ __forceinline__ void mad_wide(uint64_t& acc, uint32_t a, uint32_t b) {
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
+
+struct SqAcc {
+    uint64_t hh = 0, hl = 0, ll = 0, tiny = 0;
+    uint32_t minab = 0xFFFFFFFFu;   // min over entries of |a| bits - 1 (a zero wraps to the top)
+    __device__ __forceinline__ void add(uint32_t ab, uint32_t kbase) {   // kbase = 99 + e
+        const uint32_t E = ab >> 23;
+        const uint32_t mant = (ab & 0x7FFFFFu) | 0x800000u;   // E = 0 has k < 0: no term here
+        const uint32_t uh = __funnelshift_rc(mant, 0u, kbase + 27u - E);
+        const uint32_t ul = __funnelshift_lc(0u, mant, E - kbase) & 0x7FFFFFFu;
+        mad_wide(hh, uh, uh);
+        mad_wide(hl, uh, ul);
+        mad_wide(ll, ul, ul);
+        minab = min(minab, ab - 1u);
+    }
+    __device__ __forceinline__ bool has_small(uint32_t kbase) const { return minab < (kbase << 23) - 1u; }
+    __device__ __forceinline__ void add_small(uint32_t ab, uint32_t kbase) {   // the k < 0 terms only
+        const uint32_t E = ab >> 23;
+        const uint32_t Ee = max(E, 1u);
+        const uint32_t mant = ab - ((Ee - 1u) << 23);
+        const int k = (int)Ee - (int)kbase;
+        if (k < 0 && k > -24) tiny += ((uint64_t)mant * mant) >> (-2 * k);
+    }
+    __device__ __forceinline__ u128 sums() const { return ((u128)hh << 54) + ((u128)hl << 28) + (u128)ll; }
+    __device__ __forceinline__ void clear_sums() { hh = hl = ll = 0; }
+};
+
+struct SqAccWide {
+    u128 acc = 0;
+    __device__ __forceinline__ void add(uint32_t ab, int kbase) {   // kbase = 99 + e
+        const uint32_t E = ab >> 23;
+        const uint32_t Ee = max(E, 1u);
+        const uint32_t mant = ab - ((Ee - 1u) << 23);
+        const int k = (int)Ee - kbase;
+        if (k >= 0) {
+            const u128 U = (u128)mant << k;   // below 2^51
+            acc += U * U;
+        } else if (k > -24) {
+            acc += ((uint64_t)mant * mant) >> (-2 * k);
+        }
+    }
+};
 
 __device__ __forceinline__ int bitlen128(u128 v) {
     const uint64_t hi = (uint64_t)(v >> 64), lo = (uint64_t)v;
@@ -145,42 +206,202 @@ __global__ void __launch_bounds__(256) row_weight_kernel(const uint8_t* __restri
                 if (mx != 0) atomicCAS(&ws.info->status, 0, RK_EINVAL);
                 ws.R[i] = 0;
                 ws.e[i] = 0;
-                ws.inv[i] = 0.0f;
             }
             continue;
         }
         const int e = frexp_exp_of_absbits(mx);
         u128 acc = 0;
+        if (e >= -90) {
+            const uint32_t kbase = (uint32_t)(99 + e);
+            SqAcc sa;
+            int since = 0;   // chunks in the sums since they were folded into acc (at most 32: 512 entries)
 #pragma unroll 4
-        for (int64_t c = lane; c < nchunks; c += 32) {
-            float v[LD::kPerChunk];
-            LD::decode(__ldg(row + c), sc, v);
+            for (int64_t c = lane; c < nchunks; c += 32) {
+                float v[LD::kPerChunk];
+                LD::decode(__ldg(row + c), sc, v);
 #pragma unroll
-            for (int k = 0; k < LD::kPerChunk; ++k) {
-                if (c * LD::kPerChunk + k < n) acc += scaled_square(__float_as_uint(v[k]) & 0x7FFFFFFFu, e);
+                for (int k = 0; k < LD::kPerChunk; ++k)
+                    if (c * LD::kPerChunk + k < n) sa.add(__float_as_uint(v[k]) & 0x7FFFFFFFu, kbase);
+                if (++since == 32) {
+                    acc += sa.sums();
+                    sa.clear_sums();
+                    since = 0;
+                }
             }
+            if (sa.has_small(kbase)) {   // entries far below the largest: their floors (rare)
+                for (int64_t c = lane; c < nchunks; c += 32) {
+                    float v[LD::kPerChunk];
+                    LD::decode(__ldg(row + c), sc, v);
+#pragma unroll
+                    for (int k = 0; k < LD::kPerChunk; ++k)
+                        if (c * LD::kPerChunk + k < n) sa.add_small(__float_as_uint(v[k]) & 0x7FFFFFFFu, kbase);
+                }
+            }
+            acc += sa.sums() + (u128)sa.tiny;
+        } else {   // the largest entry is below 2^-91
+            SqAccWide sw;
+            for (int64_t c = lane; c < nchunks; c += 32) {
+                float v[LD::kPerChunk];
+                LD::decode(__ldg(row + c), sc, v);
+#pragma unroll
+                for (int k = 0; k < LD::kPerChunk; ++k)
+                    if (c * LD::kPerChunk + k < n) sw.add(__float_as_uint(v[k]) & 0x7FFFFFFFu, 99 + e);
+            }
+            acc = sw.acc;
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) acc += shfl_xor_u128(acc, o);
         if (lane == 0) {
             ws.R[i] = acc;
             ws.e[i] = e;
-            const double rd = (double)(uint64_t)(acc >> 64) * 18446744073709551616.0 + (double)(uint64_t)acc;
-            const double w2 = ldexp(rd, 2 * e - 102);
-            ws.inv[i] = (float)(1.0 / w2);
             atomicMax(&ws.info->H, bitlen128(acc) + 2 * e - 102);
         }
     }
 }
 
-// K_i = R_i >> (L + 102 - 2 e_i); L = H + ceil(log2 m) - 62.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// The same weights with one CTA per row and S rows of the CTA (rows blockIdx.x,
+// + gridDim.x, ...) in flight: every thread copies its own 16-byte chunks (tid,
+// tid + NT, ...) of a row into a shared-memory stage with cp.async and reads
+// back only those chunks, so the ring needs no barrier and no wait on another
+// thread.  The two passes (max |a|, then the exact sum) read the stage, so A is
+// read from DRAM once.  Bytes past n in the last chunk are zeroed before
+// decoding.
+template <class LD, int NT, int S>
+__global__ void __launch_bounds__(NT) row_weight_staged_kernel(const uint8_t* __restrict__ A,
+                                                               const float* __restrict__ row_scale,
+                                                               int64_t m, int64_t n, int64_t lda_bytes,
+                                                               SetupWs ws) {
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) uint4 stage[];
+    __shared__ uint32_t s_max[2][NW];
+    __shared__ uint64_t s_hi[2][NW], s_lo[2][NW];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nchunks = (int)((n + LD::kPerChunk - 1) / LD::kPerChunk);
+    const int tail_bytes = (int)(n % LD::kPerChunk) * LD::kBytes;   // 0: the last chunk is full
+    const bool owns_tail = tail_bytes && tid < nchunks && (nchunks - 1 - tid) % NT == 0;
+    const int64_t G = gridDim.x;
+    const int64_t J = (m - 1 - blockIdx.x) / G + 1;   // rows of this CTA (gridDim.x <= m)
+    auto issue = [&](int64_t j) {
+        if (j < J) {
+            const uint4* src = reinterpret_cast<const uint4*>(A + (blockIdx.x + j * G) * lda_bytes);
+            uint4* dst = stage + (size_t)(j % S) * nchunks;
+            for (int idx = tid; idx < nchunks; idx += NT) cp_async16(dst + idx, src + idx);
+        }
+        cp_async_commit();   // one group a row (empty past the last row)
+    };
+#pragma unroll
+    for (int j = 0; j < S - 1; ++j) issue(j);
+    int par = 0;
+    for (int64_t j = 0; j < J; ++j, par ^= 1) {
+        issue(j + S - 1);         // into the stage this thread finished reading in iteration j - 1
+        cp_async_wait<S - 1>();   // this thread's chunks of row j have landed
+        const int64_t i = blockIdx.x + j * G;
+        uint4* row = stage + (size_t)(j % S) * nchunks;
+        const float sc = row_scale ? __ldg(row_scale + i) : 1.0f;
+        if (owns_tail) {
+            const uint4 c = row[nchunks - 1];
+            uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int keep = tail_bytes - 4 * q;   // bytes of word q that lie inside the row
+                if (keep <= 0) w[q] = 0u;
+                else if (keep < 4) w[q] &= (1u << (8 * keep)) - 1u;
+            }
+            row[nchunks - 1] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        uint32_t mx = 0;
+#pragma unroll 4
+        for (int idx = tid; idx < nchunks; idx += NT) mx = max(mx, LD::max_abs_bits(row[idx], sc));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_max[par][wid] = mx;
+        __syncthreads();
+        mx = s_max[par][0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) mx = max(mx, s_max[par][w]);
+        if (mx >= 0x7F800000u || mx == 0) {  // inf or nan: no law; zero row: weight 0
+            if (tid == 0) {
+                if (mx != 0) atomicCAS(&ws.info->status, 0, RK_EINVAL);
+                ws.R[i] = 0;
+                ws.e[i] = 0;
+            }
+            continue;
+        }
+        const int e = frexp_exp_of_absbits(mx);
+        u128 mine;
+        if (e >= -90) {
+            const uint32_t kbase = (uint32_t)(99 + e);
+            SqAcc sa;   // at most 16 entries a chunk and 16 chunks a thread: 256 entries
+#pragma unroll 4
+            for (int idx = tid; idx < nchunks; idx += NT) {
+                float v[LD::kPerChunk];
+                LD::decode(row[idx], sc, v);
+#pragma unroll
+                for (int q = 0; q < LD::kPerChunk; ++q) sa.add(__float_as_uint(v[q]) & 0x7FFFFFFFu, kbase);
+            }
+            if (sa.has_small(kbase)) {   // entries far below the largest: their floors (rare)
+                for (int idx = tid; idx < nchunks; idx += NT) {
+                    float v[LD::kPerChunk];
+                    LD::decode(row[idx], sc, v);
+#pragma unroll
+                    for (int q = 0; q < LD::kPerChunk; ++q)
+                        sa.add_small(__float_as_uint(v[q]) & 0x7FFFFFFFu, kbase);
+                }
+            }
+            mine = sa.sums() + (u128)sa.tiny;
+        } else {   // the largest entry is below 2^-91
+            SqAccWide sw;
+            for (int idx = tid; idx < nchunks; idx += NT) {
+                float v[LD::kPerChunk];
+                LD::decode(row[idx], sc, v);
+#pragma unroll
+                for (int q = 0; q < LD::kPerChunk; ++q) sw.add(__float_as_uint(v[q]) & 0x7FFFFFFFu, 99 + e);
+            }
+            mine = sw.acc;
+        }
+        uint64_t hi = (uint64_t)(mine >> 64), lo = (uint64_t)mine;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const uint64_t ol = __shfl_xor_sync(0xffffffffu, (unsigned long long)lo, o);
+            const uint64_t oh = __shfl_xor_sync(0xffffffffu, (unsigned long long)hi, o);
+            lo += ol;
+            hi += oh + (lo < ol ? 1ull : 0ull);
+        }
+        if (lane == 0) {
+            s_hi[par][wid] = hi;
+            s_lo[par][wid] = lo;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            u128 acc = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) acc += ((u128)s_hi[par][w] << 64) | s_lo[par][w];
+            ws.R[i] = acc;
+            ws.e[i] = e;
+            atomicMax(&ws.info->H, bitlen128(acc) + 2 * e - 102);
+        }
+    }
+    cp_async_wait<0>();
+}
+
+// K_i = R_i >> (L + 102 - 2 e_i); L = H + ceil(log2 m) - 62; and
+// inv_i = 1 / ||A_i||^2 in float32 (0 for a zero row).
 __global__ void weights_to_k_kernel(int64_t m, SetupWs ws) {
     const int H = ws.info->H;
     if (H == kNoRows) {  // all rows zero: no law
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ws.info->status, 0, RK_EINVAL);
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-             i += (int64_t)gridDim.x * blockDim.x)
+             i += (int64_t)gridDim.x * blockDim.x) {
             ws.K[i] = 0;
+            ws.inv[i] = 0.0f;
+        }
         return;
     }
     int c = 0;
@@ -191,11 +412,17 @@ __global__ void weights_to_k_kernel(int64_t m, SetupWs ws) {
          i += (int64_t)gridDim.x * blockDim.x) {
         const u128 R = ws.R[i];
         uint64_t K = 0;
+        float inv = 0.0f;
         if (R != 0) {
-            const int sh = L + 102 - 2 * ws.e[i];
+            const int e = ws.e[i];
+            const int sh = L + 102 - 2 * e;
             K = (sh >= 128) ? 0 : (uint64_t)(R >> sh);  // sh >= 0 by construction of L
+            // 1 / ||A_i||^2 with ||A_i||^2 = R 2^(2e - 102) (R rounded to double once)
+            const double rd = (double)(uint64_t)(R >> 64) * 18446744073709551616.0 + (double)(uint64_t)R;
+            inv = (float)(1.0 / ldexp(rd, 2 * e - 102));
         }
         ws.K[i] = K;
+        ws.inv[i] = inv;
     }
 }
 
@@ -416,6 +643,38 @@ static int grid_for(int64_t m, int threads) {
     return (int)(g < 1 ? 1 : g);
 }
 
+template <class LD, int NT, int S>
+static void launch_row_weight_staged(const uint8_t* A, const float* row_scale, int64_t m, int64_t n,
+                                     int64_t lda_bytes, const SetupWs& ws, int sms, cudaStream_t st) {
+    const int64_t nchunks = (n + LD::kPerChunk - 1) / LD::kPerChunk;
+    const size_t smem = (size_t)S * (size_t)nchunks * 16;
+    auto kern = row_weight_staged_kernel<LD, NT, S>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    const int g = (int)std::min<int64_t>(m, (int64_t)sms * (per_sm < 1 ? 1 : per_sm));
+    kern<<<g, NT, smem, st>>>(A, row_scale, m, n, lda_bytes, ws);
+}
+
+// Rows of more than 8 KB and up to 64 KB go to the staged CTA-per-row kernel
+// (read once through a ring of cp.async stages, up to 128 KB a CTA); shorter
+// rows (a warp a row re-reads them from L2 and needs no CTA barrier) and longer
+// ones to the warp-per-row kernel.
+template <class LD>
+static void launch_row_weights(const uint8_t* A, const float* row_scale, int64_t m, int64_t n,
+                               int64_t lda_bytes, const SetupWs& ws, int sms, cudaStream_t st) {
+    const int64_t nchunks = (n + LD::kPerChunk - 1) / LD::kPerChunk;
+    const int64_t row_bytes = nchunks * 16;
+    if (row_bytes > 8 * 1024 && row_bytes <= 64 * 1024) {
+        if (row_bytes <= 12 * 1024) launch_row_weight_staged<LD, 256, 8>(A, row_scale, m, n, lda_bytes, ws, sms, st);
+        else if (row_bytes <= 24 * 1024) launch_row_weight_staged<LD, 256, 4>(A, row_scale, m, n, lda_bytes, ws, sms, st);
+        else launch_row_weight_staged<LD, 256, 2>(A, row_scale, m, n, lda_bytes, ws, sms, st);
+        return;
+    }
+    const int gw = (int)std::min<int64_t>((m + 7) / 8, (int64_t)sms * 8);   // 8 rows (warps) a CTA
+    row_weight_kernel<LD><<<gw, 256, 0, st>>>(A, row_scale, m, n, lda_bytes, ws);
+}
+
 __global__ void setup_info_init_kernel(SetupInfo* info) {
     SetupInfo init{};
     init.H = kNoRows;
@@ -430,17 +689,16 @@ int launch_setup(const void* A, rk_dtype dt, const float* row_scale, int64_t m, 
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int gw = (int)std::min<int64_t>((m + 7) / 8, (int64_t)sms * 8);   // 8 rows (warps) a CTA
     const uint8_t* Ab = static_cast<const uint8_t*>(A);
     switch (dt) {
         case RK_F32:
-            row_weight_kernel<LoadF32><<<gw, 256, 0, st>>>(Ab, nullptr, m, n, lda * 4, ws);
+            launch_row_weights<LoadF32>(Ab, nullptr, m, n, lda * 4, ws, sms, st);
             break;
         case RK_BF16:
-            row_weight_kernel<LoadBF16><<<gw, 256, 0, st>>>(Ab, nullptr, m, n, lda * 2, ws);
+            launch_row_weights<LoadBF16>(Ab, nullptr, m, n, lda * 2, ws, sms, st);
             break;
         case RK_FP8E4M3:
-            row_weight_kernel<LoadFP8><<<gw, 256, 0, st>>>(Ab, row_scale, m, n, lda, ws);
+            launch_row_weights<LoadFP8>(Ab, row_scale, m, n, lda, ws, sms, st);
             break;
     }
     count_launch();

@@ -81,6 +81,40 @@ def test_tables_bit_exact(rk, case):
     _check_tables(rk, A)
 
 
+@pytest.mark.parametrize("m,n,special", [
+    (600, 1025, "ragged"),        # 4 KB rows, a 1-element tail chunk (a warp a row)
+    (500, 2500, "ragged"),        # 10 KB rows (a CTA a row, 8 rows in flight)
+    (300, 4096, "zerorows"),      # 16 KB rows (a CTA a row, 4 in flight)
+    (300, 4097, "skewed"),        # a 1-element tail chunk
+    (200, 10000, "tiny_values"),  # 40 KB rows (2 in flight); rows whose largest entry is subnormal
+    (120, 16384, "plain"),        # 64 KB rows, the longest staged in shared memory
+    (90, 16387, "ragged"),        # past 64 KB rows: a warp a row again
+])
+def test_tables_bit_exact_long_rows(rk, m, n, special):
+    """Sampling tables of rows long enough for the CTA-per-row setup kernel (rows
+    staged in shared memory), bit-exact against the oracle."""
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    if special == "zerorows":
+        A[::7] = 0
+    elif special == "skewed":
+        A *= (10.0 ** rng.uniform(-2, 2, size=(m, 1))).astype(np.float32)
+    elif special == "tiny_values":
+        A[::3] = (A[::3] * 1e-41).astype(np.float32)   # subnormal rows
+        A[1::3, :5] *= np.float32(1e30)                   # the rest of the row floors to 0
+        A[2::3, :3] *= np.float32(2.0 ** 20)              # entries below 2^-5 floor to nonzero terms
+    _check_tables(rk, A)
+
+
+@pytest.mark.parametrize("n", [9, 3000])
+def test_setup_rejects_nonfinite_entries(rk, n):
+    for bad in (float("nan"), float("inf")):
+        B = torch.randn((64, n), device="cuda")
+        B[37, n // 2] = bad
+        with pytest.raises(rk.RkError):
+            rk.rk_setup(rk.aligned_rows(B)).status()
+
+
 def test_setup_rejects_zero_and_nonfinite(rk):
     A = torch.zeros((64, 8), device="cuda")
     plan = rk.rk_setup(A)

@@ -48,7 +48,14 @@ def test_quantizers_bit_exact(rk, sysm):
 
 
 @pytest.mark.parametrize("kind", ["bf16", "fp8"])
-def test_stored_row_tables_bit_exact(rk, sysm, kind):
+@pytest.mark.parametrize("shape", [None, (400, 2600), (300, 4100), (250, 9000), (120, 30000),
+                                   (100, 60000)])
+def test_stored_row_tables_bit_exact(rk, sysm, kind, shape):
+    """Short rows (a warp a row) and rows of 8 KB to 64 KB in the stored type (a CTA a
+    row, staged in shared memory), bit-exact against the oracle."""
+    if shape is not None:
+        m, n = shape
+        sysm = rk_inputs.gaussian_system(m, n, seed=m + n)
     A = rk.aligned_rows(_dev(sysm.A))
     Aq, sc = rk.quantize(A, kind)
     plan = rk.rk_setup(Aq, kind, sc)
