@@ -76,7 +76,7 @@ def lib():
                                ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                _u64p, _u32p, ctypes.c_int, ctypes.c_int, _f64p, ctypes.c_double,
                                _i64p, _f64p]
-        L.orc_rkab_ext.argtypes = L.orc_rkab.argtypes + [ctypes.c_int, _u64p, _f64p]
+        L.orc_rkab_ext.argtypes = L.orc_rkab.argtypes + [ctypes.c_int, _u64p, _f64p, _f64p]
         L.orc_select_row.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                      ctypes.c_int, ctypes.c_uint32, ctypes.c_int64, _u64p, _u32p,
                                      _u64p]
@@ -233,9 +233,10 @@ def rka_formula(A, b, x0, q, iters, seed, tab: Table, stream=0, omega=1.0):
 
 def rkab(A, b, x0, q, alpha, rounds, seed, tab: Table, round0=0, stream=0, omega=1.0,
          same_stream=False, threads=1, x_ref=None, tol=0.0, want_trace=False, sampling="full",
-         row_weight=None):
+         row_weight=None, worker_weight=None):
     """RKAB rounds; returns x (and rounds done, trace of rel. errors if x_ref given).
-    sampling: row selection ('full', 'blocks', 'cyclic'); row_weight: w_i of Eq. (rka_eq)."""
+    sampling: row selection ('full', 'blocks', 'cyclic'); row_weight: w_i of Eq. (rka_eq);
+    worker_weight: q per-worker weights (the Partial Matrix alpha of Section 3.3.1)."""
     A, m, n, lda = _mat(A)
     b = _vec64(b, m)
     x0 = _vec64(x0, n)
@@ -246,12 +247,14 @@ def rkab(A, b, x0, q, alpha, rounds, seed, tab: Table, round0=0, stream=0, omega
     mode = SAMPLING[sampling] if isinstance(sampling, str) else int(sampling)
     K = np.ascontiguousarray(tab.K, np.uint64)
     wv = None if row_weight is None else _vec64(row_weight, m)
+    uv = None if worker_weight is None else _vec64(worker_weight, q)
     _check(lib().orc_rkab_ext(_p(A, _f32p), m, n, lda, _p(b, _f64p), _p(x0, _f64p), _p(x, _f64p),
                               q, alpha, rounds, round0, seed, stream, omega, _p(tab.thr64, _u64p),
                               _p(tab.alias, _u32p), int(bool(same_stream)), threads,
                               None if xr is None else _p(xr, _f64p), tol, ctypes.byref(done),
                               None if trace is None else _p(trace, _f64p), mode, _p(K, _u64p),
-                              None if wv is None else _p(wv, _f64p)), "rkab")
+                              None if wv is None else _p(wv, _f64p),
+                              None if uv is None else _p(uv, _f64p)), "rkab")
     if want_trace:
         return x, int(done.value), trace[: int(done.value)]
     if xr is not None:
@@ -417,6 +420,30 @@ def spectrum(A):
     A64 = np.asarray(A, np.float64)
     sv = np.linalg.svd(A64, compute_uv=False)
     return float(sv[-1] ** 2), float(sv[0] ** 2), float(np.sum(A64 * A64))
+
+
+def block_bounds(m, q, g):
+    """Rows [lo, hi) of worker g's block in the Distributed Approach (Section 3.3.1):
+    lo = floor(g m / q), hi = floor((g + 1) m / q)."""
+    return (g * m) // q, ((g + 1) * m) // q
+
+
+def partial_alpha_star(A, q):
+    """The Partial Matrix alpha of Section 3.3.1 (Table 1): for each worker g, Eq.
+    (best_alpha) with q workers and s_min, s_max of its own block A_g (the Distributed
+    Approach's rows), s = sigma^2(A_g) / ||A_g||_F^2 over the min(m_g, n) singular values
+    of A_g (LAPACK SVD through `spectrum`).  Returns (alphas (q,), spectra (q, 3))."""
+    A = np.asarray(A)
+    m = A.shape[0]
+    if not 1 <= q <= m:
+        raise ValueError("1 <= q <= m")
+    al = np.zeros(q)
+    sp = np.zeros((q, 3))
+    for g in range(q):
+        lo, hi = block_bounds(m, q, g)
+        sp[g] = spectrum(A[lo:hi])
+        al[g] = alpha_star(q, sp[g, 0] / sp[g, 2], sp[g, 1] / sp[g, 2])
+    return al, sp
 
 
 def alpha_star(q, s_min, s_max):

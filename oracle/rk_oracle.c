@@ -25,8 +25,9 @@
  *   orc_rka_formula     RKA iteration written as Eq. (rka_uni_weights)
  *   orc_rkab            RKAB (Section 3.4.1, Algorithm 3): q workers, alpha
  *                       projections each, then the average
- *   orc_rkab_ext        the same with a row selection and per-row weights w_i of
- *                       Eq. (rka_eq)
+ *   orc_rkab_ext        the same with a row selection, per-row weights w_i of
+ *                       Eq. (rka_eq) and per-worker weights (the Partial Matrix
+ *                       alpha of Section 3.3.1)
  *   orc_residual        r = b - A x, ||r||, ||A^T r||
  *   orc_bf16_rne        FP32 -> BF16 round-to-nearest-even
  *   orc_fp8e4m3_rne     FP32 -> FP8 e4m3 (OCP "fn" variant) round-to-nearest-even,
@@ -387,13 +388,18 @@ int orc_rka_formula(const float *A, int64_t m, int64_t n, int64_t lda, const dou
 /* average when x_ref != NULL.  Workers run in parallel on `threads` OpenMP  */
 /* threads (the shared-memory structure of Algorithm 3); the result does not */
 /* depend on the thread count.                                              */
+/*                                                                           */
+/* Weights: a projection of row i by worker gamma uses the relaxation        */
+/* omega * w_i * u_gamma, w_i = row_weight[i] (Eq. (rka_eq)), u_gamma =      */
+/* worker_weight[gamma] (a per-thread alpha, Section 3.3.1); NULL means 1.   */
 /* ------------------------------------------------------------------------- */
 int orc_rkab_ext(const float *A, int64_t m, int64_t n, int64_t lda, const double *b,
                  const double *x0, double *x, int q, int64_t alpha, int64_t rounds,
                  int64_t round0, uint64_t seed, uint32_t stream, double omega,
                  const uint64_t *thr64, const uint32_t *alias, int same_stream, int threads,
                  const double *x_ref, double tol, int64_t *rounds_done, double *trace,
-                 int sampling, const uint64_t *K, const double *row_weight)
+                 int sampling, const uint64_t *K, const double *row_weight,
+                 const double *worker_weight)
 {
     if (q < 1 || alpha < 1 || rounds < 0) return ORC_EINVAL;
     if (sampling != 0 && (same_stream || (sampling == 1 && !K))) return ORC_EINVAL;
@@ -413,12 +419,13 @@ int orc_rkab_ext(const float *A, int64_t m, int64_t n, int64_t lda, const double
             double *v = V + (size_t)g * (size_t)n;
             memcpy(v, x, sizeof(double) * (size_t)n);
             uint32_t worker = same_stream ? 0u : (uint32_t)g;
+            double ug = worker_weight ? worker_weight[g] : 1.0;
             for (int64_t j = 0; j < alpha; ++j) {
                 uint64_t t = (uint64_t)(round * alpha + j);
                 int64_t i = orc_select_row(sampling, seed, t, worker, q, stream, m, thr64, alias, K);
                 if (i < 0) continue;   /* a block of weight 0 (reported by the caller) */
                 double wi = row_weight ? row_weight[i] : 1.0;
-                project(A + i * lda, b[i], w[i], omega * wi, v, n);
+                project(A + i * lda, b[i], w[i], omega * wi * ug, v, n);
             }
         }
         for (int64_t j = 0; j < n; ++j) {
@@ -447,7 +454,7 @@ int orc_rkab(const float *A, int64_t m, int64_t n, int64_t lda, const double *b,
 {
     return orc_rkab_ext(A, m, n, lda, b, x0, x, q, alpha, rounds, round0, seed, stream, omega,
                         thr64, alias, same_stream, threads, x_ref, tol, rounds_done, trace, 0,
-                        NULL, NULL);
+                        NULL, NULL, NULL);
 }
 
 /* Worker iterates of one RKAB round (before the average), for the Jensen
