@@ -95,6 +95,11 @@ typedef struct {
                                                the cyclic Kaczmarz method for q = 1)   [FULL] */
     const float *row_weight;  /* device, m floats or NULL: per-row weights w_i of Eq.
                               (rka_eq), multiplying omega in each projection        [NULL]*/
+    const float *worker_weight; /* device, q floats or NULL: per-worker weights, the
+                              Partial Matrix alpha of Section 3.3.1 (Table 1): every
+                              projection of worker g is scaled by worker_weight[g],
+                              multiplying omega and the row weight
+                              (rk_partial_alpha_star computes them)                [NULL]*/
 } rk_opts;
 
 /* Row selection of rk_opts.sampling. */
@@ -388,19 +393,37 @@ double rk_alpha_star(int q, double s_min, double s_max);
 /* Bytes of device workspace rk_spectrum needs for k Lanczos steps. */
 size_t rk_spectrum_workspace_bytes(int64_t m, int64_t n, int k);
 
-/* Estimates of the extreme eigenvalues of A^T A (sigma_min^2, sigma_max^2) and ||A||_F^2
- * for device float32 A (m x n, lda; 16-byte aligned rows): k steps (1 <= k <= 512, at most
- * n used) of the symmetric Lanczos process on A^T A from a start vector drawn with
- * Philox4x32-10 (key = seed), with full reorthogonalisation in float64; each step applies
- * A^T A as two passes over A.  The end eigenvalues of the k x k tridiagonal matrix
- * satisfy lambda_min <= out[0] and out[1] <= lambda_max up to rounding (equality once the
- * process spans the space, e.g. k >= n).
- *   out   host, 3 doubles <- [lambda_min estimate, lambda_max estimate, ||A||_F^2]
+/* Estimates of the extreme squared singular values of A (sigma_min^2, sigma_max^2 over
+ * the min(m, n) singular values) and ||A||_F^2 for device float32 A (m x n, lda; 16-byte
+ * aligned rows): k steps (1 <= k <= 512, at most min(m, n) used) of the symmetric Lanczos
+ * process with full reorthogonalisation in float64, from a start vector drawn with
+ * Philox4x32-10 (key = seed).  For m >= n it runs on A^T A, each step one pass over A
+ * (one round of the RKA kernel over all rows; two passes when the rows are too long for
+ * it); for m < n on A A^T (the same nonzero eigenvalues without the n - m zero ones of
+ * A^T A), each step an A^T u pass and an A y pass.  The end eigenvalues of the
+ * tridiagonal matrix satisfy sigma_min^2 <= out[0] and out[1] <= sigma_max^2 up to
+ * rounding (equality once the process spans the space, e.g. k >= min(m, n)).
+ *   out   host, 3 doubles <- [sigma_min^2 estimate, sigma_max^2 estimate, ||A||_F^2]
  *   steps_done  host (may be NULL) <- Lanczos steps taken (fewer than k on breakdown)
  *   workspace   device, >= rk_spectrum_workspace_bytes(m, n, k), 256-byte aligned
  * Synchronous: waits for `stream` once per step. */
 int rk_spectrum(const float *A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed,
                 void *workspace, size_t ws_bytes, void *stream, double *out, int *steps_done);
+
+/* Bytes of device workspace rk_partial_alpha_star needs. */
+size_t rk_partial_alpha_workspace_bytes(int64_t m, int64_t n, int q, int k);
+
+/* The Partial Matrix alpha of Section 3.3.1 (Table 1): for each worker g of q, alpha* of
+ * Eq. (best_alpha) with q workers and s_min, s_max of its own row block A_g (rows
+ * floor(g m / q) .. floor((g+1) m / q) - 1, the blocks of the Distributed Approach),
+ * s = sigma^2(A_g) / ||A_g||_F^2, the extremes estimated by rk_spectrum(A_g, k, seed).
+ * Pass the weights to rk_opts.worker_weight (after copying them to the device).
+ *   weights  host, q floats <- the per-worker alpha
+ *   spectra  host, 3 q doubles or NULL <- rk_spectrum's out[] of every block
+ * RK_EINVAL when q < 1 or q > m (an empty block).  Synchronous, like rk_spectrum. */
+int rk_partial_alpha_star(const float *A, int64_t m, int64_t n, int64_t lda, int q, int k,
+                          uint64_t seed, void *workspace, size_t ws_bytes, void *stream,
+                          float *weights, double *spectra);
 
 /* Name of an error code. */
 const char *rk_strerror(int code);

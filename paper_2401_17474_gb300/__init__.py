@@ -20,6 +20,7 @@ from .api import (  # noqa: F401
     launch_count,
     make_opts,
     optimal_weight,
+    partial_alpha_star,
     quantize,
     rank2,
     rk_residual,

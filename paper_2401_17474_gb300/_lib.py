@@ -41,6 +41,7 @@ class RkOpts(ctypes.Structure):
         ("lookahead", ctypes.c_int),
         ("sampling", ctypes.c_int),
         ("row_weight", ctypes.c_void_p),
+        ("worker_weight", ctypes.c_void_p),
     ]
 
 
@@ -106,6 +107,11 @@ _SIG = {
     "rk_spectrum": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                    ctypes.c_uint64, _V, ctypes.c_size_t, _V,
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "rk_partial_alpha_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                                           ctypes.c_int]),
+    "rk_partial_alpha_star": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_uint64, _V, ctypes.c_size_t, _V,
+                                             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)]),
     "rk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "rk_launch_count": (ctypes.c_uint64, []),
 }

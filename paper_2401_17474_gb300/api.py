@@ -152,7 +152,7 @@ SAMPLING = {"full": 0, "blocks": 1, "cyclic": 2}
 
 def make_opts(omega=1.0, check_every=1, tol=0.0, x_ref=None, round0=0, stream_id=0,
               same_stream=False, cluster_size=0, timeout_s=10.0, lookahead=0,
-              sampling="full", row_weight=None) -> RkOpts:
+              sampling="full", row_weight=None, worker_weight=None) -> RkOpts:
     o = RkOpts()
     _lib.load().rk_opts_default(ctypes.byref(o))
     o.omega = float(omega)
@@ -168,6 +168,7 @@ def make_opts(omega=1.0, check_every=1, tol=0.0, x_ref=None, round0=0, stream_id
     o.lookahead = int(lookahead)
     o.sampling = SAMPLING[sampling] if isinstance(sampling, str) else int(sampling)
     o.row_weight = None if row_weight is None else row_weight.data_ptr()
+    o.worker_weight = None if worker_weight is None else worker_weight.data_ptr()
     return o
 
 
@@ -206,11 +207,13 @@ def _vec(t, n, name):
 def rkab_solve(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, rounds: int = 1,
                seed: int = 0, *, omega=1.0, x_ref=None, tol=0.0, check_every=1, round0=0,
                stream_id=0, same_stream=False, timeout_s=10.0, lookahead=0, cluster_size=0,
-               sampling="full", row_weight=None, out=None, solver=None, stream=None,
-               raise_on_error=True):
+               sampling="full", row_weight=None, worker_weight=None, out=None, solver=None,
+               stream=None, raise_on_error=True):
     """RKAB solve (alpha projections per worker between averages); returns (x, info).
     sampling: 'full' (Eq. (prob_line)), 'blocks' (per-worker row blocks), 'cyclic';
-    row_weight: optional per-row weights w_i (m floats on the device)."""
+    row_weight: optional per-row weights w_i (m floats on the device);
+    worker_weight: optional per-worker weights (q floats on the device), e.g. the
+    Partial Matrix alpha of `partial_alpha_star`."""
     b = _vec(b, plan.m, "b")
     if x0 is None:
         x0 = torch.zeros(plan.n, dtype=torch.float32, device=plan.device)
@@ -221,8 +224,10 @@ def rkab_solve(plan: Plan, b, x0=None, q: int = 1, alpha: int = 1, rounds: int =
     s = solver if solver is not None else Solver(plan, q)
     if row_weight is not None:
         row_weight = _vec(row_weight, plan.m, "row_weight")
+    if worker_weight is not None:
+        worker_weight = _vec(worker_weight, s.q, "worker_weight")
     opts = make_opts(omega, check_every, tol, x_ref, round0, stream_id, same_stream, cluster_size,
-                     timeout_s, lookahead, sampling, row_weight)
+                     timeout_s, lookahead, sampling, row_weight, worker_weight)
     s.launch(b, x0, x, alpha, rounds, seed, opts, stream)
     info = s.info(stream)
     if raise_on_error and info.status != _lib.RK_OK:
@@ -399,6 +404,27 @@ def optimal_weight(A: torch.Tensor, q: int, k: int = 32, seed: int = 0, stream=N
     """(alpha*, Spectrum): the weight of Eq. (best_alpha) for RKA with q workers on A."""
     sp = spectrum(A, k, seed, stream)
     return alpha_star(q, sp.s_min, sp.s_max), sp
+
+
+def partial_alpha_star(A: torch.Tensor, q: int, k: int = 8, seed: int = 0, stream=None):
+    """The Partial Matrix alpha of Section 3.3.1 (rk_partial_alpha_star): for each worker g
+    of q, alpha* of Eq. (best_alpha) from the spectrum of its own row block (the
+    Distributed Approach's rows), each estimated by k Lanczos steps.  Returns
+    (weights: q float32 on A's device, for `worker_weight`; list of Spectrum)."""
+    if A.dtype != torch.float32 or A.stride(1) != 1 or not A.is_cuda:
+        raise ValueError("A must be a float32 CUDA matrix with unit column stride")
+    m, n = A.shape
+    lib = _lib.load()
+    nbytes = lib.rk_partial_alpha_workspace_bytes(m, n, int(q), int(k))
+    if nbytes == 0:
+        raise RkError(_lib.RK_EINVAL, "rk_partial_alpha_workspace_bytes")
+    ws = _workspace(nbytes, A.device)
+    w = (ctypes.c_float * int(q))()
+    sp = (ctypes.c_double * (3 * int(q)))()
+    check(lib.rk_partial_alpha_star(_ptr(A), m, n, A.stride(0), int(q), int(k), int(seed), _ptr(ws),
+                                    ws.numel(), _stream(stream), w, sp), "rk_partial_alpha_star")
+    weights = torch.tensor(list(w), dtype=torch.float32, device=A.device)
+    return weights, [Spectrum(sp[3 * g], sp[3 * g + 1], sp[3 * g + 2], 0) for g in range(int(q))]
 
 
 def launch_count() -> int:

@@ -88,6 +88,7 @@ void rk_opts_default(rk_opts* o) {
     o->lookahead = 0;
     o->sampling = RK_SAMPLE_FULL;
     o->row_weight = nullptr;
+    o->worker_weight = nullptr;
 }
 
 // Row selection: a known mode; per-worker modes need the workers' own streams.
@@ -464,19 +465,57 @@ double rk_alpha_star(int q, double s_min, double s_max) {
     return 2.0 * q / (1.0 + (q - 1) * (s_min + s_max));
 }
 
+static int lanczos_steps(int64_t m, int64_t n, int k) {   // at most min(m, n) are of use
+    const int64_t r = m < n ? m : n;
+    return (int)(k < r ? k : r);
+}
+
 size_t rk_spectrum_workspace_bytes(int64_t m, int64_t n, int k) {
     if (m < 1 || n < 1 || k < 1 || k > 512) return 0;
-    return spectrum_ws_bytes(m, n, (int)(k < n ? k : n));
+    return spectrum_ws_bytes(m, n, lanczos_steps(m, n, k));
 }
 
 int rk_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed,
                 void* workspace, size_t ws_bytes, void* stream, double* out, int* steps_done) {
     if (!A || !workspace || !out || m < 1 || n < 1 || lda < n || k < 1 || k > 512) return RK_EINVAL;
     if (!aligned16(A) || (lda * 4) % 16 != 0 || ((uintptr_t)workspace & 255u) != 0) return RK_EALIGN;
-    const int kk = (int)(k < n ? k : n);
+    const int kk = lanczos_steps(m, n, k);
     if (ws_bytes < spectrum_ws_bytes(m, n, kk)) return RK_EWORKSPACE;
     return run_spectrum(A, m, n, lda, kk, seed, workspace, static_cast<cudaStream_t>(stream), out,
                         steps_done);
+}
+
+size_t rk_partial_alpha_workspace_bytes(int64_t m, int64_t n, int q, int k) {
+    if (m < 1 || n < 1 || q < 1 || q > m || k < 1 || k > 512) return 0;
+    const int64_t rows = (m + q - 1) / q + 1;   // the largest block
+    return spectrum_ws_bytes(rows, n, lanczos_steps(rows, n, k));
+}
+
+int rk_partial_alpha_star(const float* A, int64_t m, int64_t n, int64_t lda, int q, int k,
+                          uint64_t seed, void* workspace, size_t ws_bytes, void* stream,
+                          float* weights, double* spectra) {
+    if (!A || !workspace || !weights || m < 1 || n < 1 || lda < n || q < 1 || q > m || k < 1 || k > 512)
+        return RK_EINVAL;
+    if (!aligned16(A) || (lda * 4) % 16 != 0 || ((uintptr_t)workspace & 255u) != 0) return RK_EALIGN;
+    if (ws_bytes < rk_partial_alpha_workspace_bytes(m, n, q, k)) return RK_EWORKSPACE;
+    for (int g = 0; g < q; ++g) {
+        // the Distributed Approach's block of worker g (Section 3.3.1)
+        const int64_t lo = (int64_t)g * m / q, hi = (int64_t)(g + 1) * m / q;
+        double out[3];
+        const int rc = run_spectrum(A + lo * lda, hi - lo, n, lda, lanczos_steps(hi - lo, n, k), seed,
+                                    workspace, static_cast<cudaStream_t>(stream), out, nullptr);
+        if (rc != RK_OK) return rc;
+        if (!(out[2] > 0.0)) return RK_EINVAL;   // a zero block has no law
+        const double s_min = std::fmin(std::fmax(out[0] / out[2], 0.0), 1.0);
+        const double s_max = std::fmin(std::fmax(out[1] / out[2], 0.0), 1.0);
+        weights[g] = (float)rk_alpha_star(q, s_min, s_max);
+        if (spectra) {
+            spectra[3 * g] = out[0];
+            spectra[3 * g + 1] = out[1];
+            spectra[3 * g + 2] = out[2];
+        }
+    }
+    return RK_OK;
 }
 
 size_t rk_residual_workspace_bytes(int64_t m, int64_t n) {

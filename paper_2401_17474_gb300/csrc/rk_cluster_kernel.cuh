@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
         const int S_ = S;
         const int64_t total_ = total;
         const uint32_t worker = p.same_stream ? 0u : (uint32_t)gamma;
+        const float ww = p.worker_weight ? __ldg(p.worker_weight + gamma) : 1.f;   // per-worker weight
         const uint64_t tbase = (uint64_t)p.round0 * (uint64_t)p.alpha;
         const uint64_t pol = policy_evict_first();
         int64_t issued = 0;
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
                 }
                 const float sc = (ELT == ELT_FP8) ? __ldg(p.row_scale + row) : 1.f;
                 const float wi = p.row_weight ? __ldg(p.row_weight + row) : 1.f;
-                pbuf[lane_] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row) * wi, sc);
+                pbuf[lane_] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row) * wi * ww, sc);
             }
             __syncwarp();
             if (lane_ == 0) {

@@ -101,6 +101,10 @@ int launch_residual(const float* A, int64_t m, int64_t n, int64_t lda, const flo
 
 int launch_normal_matvec(const float* A, int64_t m, int64_t n, int64_t lda, const float* v,
                          double* w, void* ws, cudaStream_t st);
+int launch_rows_matvec(const float* A, int64_t m, int64_t n, int64_t lda, const float* v, double* r,
+                       void* ws, cudaStream_t st);
+int launch_transpose_matvec(const float* A, int64_t m, int64_t n, int64_t lda, const double* u,
+                            double* w, void* ws, cudaStream_t st);
 size_t spectrum_ws_bytes(int64_t m, int64_t n, int k);
 int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed, void* ws,
                  cudaStream_t st, double* out, int* steps_done);

@@ -197,6 +197,7 @@ int run_refine(const Plan* lowp, const float* A32, int64_t lda32, const float* b
         io.lookahead = o.lookahead;
         io.sampling = o.sampling;
         io.row_weight = o.row_weight;
+        io.worker_weight = o.worker_weight;
         a.opts = io;
         a.info = static_cast<SolveInfo*>(w.solve_ws);
         a.ldv = (n + 3) / 4 * 4;

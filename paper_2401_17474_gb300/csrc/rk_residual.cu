@@ -295,4 +295,43 @@ int launch_normal_matvec(const float* A, int64_t m, int64_t n, int64_t lda, cons
     return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
 }
 
+// r = -A v for float32 A and v (the row pass of the residual without a right-hand
+// side), written to r (m doubles).  One pass over A.
+int launch_rows_matvec(const float* A, int64_t m, int64_t n, int64_t lda, const float* v, double* r,
+                       void* ws, cudaStream_t st) {
+    ResWs rw = carve(ws, m, n);
+    residual_rows_kernel<<<res_blocks(m), kResThreads, 0, st>>>(A, m, n, lda, nullptr, v, r, rw.rs,
+                                                                rw.rr_part);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
+}
+
+// rs_i = u_i split into float32 (hi, lo), the input format of the A^T r pass.
+__global__ void split_rows_kernel(const double* __restrict__ u, int64_t m, float2* __restrict__ rs) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float h = (float)u[i];
+        rs[i] = make_float2(h, (float)(u[i] - (double)h));
+    }
+}
+
+// w = -A^T u for float32 A and float64 u (m entries): the A^T r pass of the residual
+// with r = u, then the fixed-order sum of its row-chunk partials.  One pass over A;
+// u may share storage with w (u is consumed before w is written).
+int launch_transpose_matvec(const float* A, int64_t m, int64_t n, int64_t lda, const double* u,
+                            double* w, void* ws, cudaStream_t st) {
+    ResWs rw = carve(ws, m, n);
+    const int64_t gs = (m + kResThreads - 1) / kResThreads;
+    split_rows_kernel<<<(unsigned)(gs < 2048 ? gs : 2048), kResThreads, 0, st>>>(u, m, rw.rs);
+    count_launch();
+    const int chunks = atr_chunks(m, n);
+    dim3 grid((unsigned)((n + kAtrCols - 1) / kAtrCols), (unsigned)chunks);
+    residual_atr_kernel<<<grid, kResThreads, 0, st>>>(A, m, n, lda, rw.rs, chunks, rw.atr_part);
+    count_launch();
+    const int64_t gb = (n + kResThreads - 1) / kResThreads;
+    gather_neg_kernel<<<(unsigned)(gb < 1024 ? gb : 1024), kResThreads, 0, st>>>(rw.atr_part, chunks, n, w);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
+}
+
 }  // namespace rk

@@ -160,6 +160,7 @@ static KParams base_params(const SolveArgs& a) {
     p.sampling = a.opts.sampling;
     p.P = pl->ws.P;
     p.row_weight = a.opts.row_weight;
+    p.worker_weight = a.opts.worker_weight;
     p.q = a.q;
     p.alpha = a.alpha;
     p.rounds = a.rounds;

@@ -70,6 +70,7 @@ struct KParams {
     int sampling;           // rk_sampling: full law, per-worker row blocks, cyclic
     const uint64_t* P;      // exclusive prefix of the integer weights (row blocks)
     const float* row_weight;  // per-row weights w_i (NULL: 1)
+    const float* worker_weight;  // per-worker weights (NULL: 1)
     int jacobi;             // RKA with q workers spread over the CTAs (alpha = 1): CTA g
                             // holds workers [g q / G, (g+1) q / G), each one projection per
                             // round from the round's x; their sum is the CTA's row of V
@@ -233,9 +234,11 @@ __device__ void producer_loop(const KParams& p, uint8_t* stages, uint64_t* full,
             // worker gamma's t-th draw; with jacobi, draw j of round r belongs to
             // worker w0 + j and is its round0 + r-th projection
             uint32_t wk = worker;
+            uint32_t own = blockIdx.x;   // the worker whose projection this is
             uint64_t tt = tbase + (uint64_t)tl;
             if constexpr (JAC) {
-                wk = p.same_stream ? 0u : w0 + (uint32_t)(tl % per);
+                own = w0 + (uint32_t)(tl % per);
+                wk = p.same_stream ? 0u : own;
                 tt = (uint64_t)p.round0 + (uint64_t)(tl / per);
             }
             uint32_t row = draw_row(p, wk, tt);
@@ -244,8 +247,9 @@ __device__ void producer_loop(const KParams& p, uint8_t* stages, uint64_t* full,
                 row = 0;
             }
             const float sc = (ELT == ELT_FP8) ? __ldg(p.row_scale + row) : 1.f;
-            // a per-row weight w_i scales the projection with 1/||A_i||^2
-            const float wi = p.row_weight ? __ldg(p.row_weight + row) : 1.f;
+            // a per-row weight w_i and a per-worker weight scale the projection with 1/||A_i||^2
+            float wi = p.row_weight ? __ldg(p.row_weight + row) : 1.f;
+            if (p.worker_weight) wi *= __ldg(p.worker_weight + own);
             pbuf[lane] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row) * wi, sc);
         }
         __syncwarp();

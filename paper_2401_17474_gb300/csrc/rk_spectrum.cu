@@ -12,7 +12,9 @@
 // (n up to 20480): one round of the RKA kernel in which every row is taken once
 // (cyclic selection, q = m workers), with b = 0, unit reciprocal norms and the
 // weight -m, returns v + A^T A v in float32.  Longer rows take the two residual
-// passes (float64-class).
+// passes (float64-class).  For m < n the process runs on A A^T in R^m instead (the
+// same nonzero eigenvalues, without the n - m zero eigenvalues of A^T A): each step
+// is the A^T r pass (y = -A^T v) and the row pass (-A y).
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -257,6 +259,12 @@ __global__ void fill_kernel(float* __restrict__ a, int64_t m, float v) {
         a[i] = v;
 }
 
+__global__ void to_float_kernel(const double* __restrict__ y, int64_t n, float* __restrict__ yf) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        yf[j] = (float)y[j];
+}
+
 // w = vout - v in float64 (vout = v + A^T A v from the one-pass operator).
 __global__ void diff_kernel(const float* __restrict__ vout, const float* __restrict__ v, int64_t n,
                             double* __restrict__ w) {
@@ -307,10 +315,15 @@ int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint6
     fro_rows_kernel<<<fb, kSpThreads, 0, st>>>(A, m, n, lda, w.fpart);
     sum_parts_kernel<<<1, 32, 0, st>>>(w.fpart, fb, w.scal + 1);
     count_launch(2);
+    // the process runs on A^T A in R^n, or for m < n on A A^T in R^m: the same nonzero
+    // eigenvalues without the n - m zero ones, which rounding would otherwise bring in
+    // (a well separated end of the spectrum, found within a few steps)
+    const bool wide = m < n;
+    const int64_t d = wide ? m : n;
     // v_0: seeded start vector, normalised
-    lanczos_start_kernel<<<grid_for(n), kSpThreads, 0, st>>>(w.w, n, seed);
-    norm2_kernel<<<1, kSpThreads, 0, st>>>(w.w, n, w.scal);
-    scale_kernel<<<grid_for(n), kSpThreads, 0, st>>>(w.w, n, w.scal, w.V, w.vf);
+    lanczos_start_kernel<<<grid_for(d), kSpThreads, 0, st>>>(w.w, d, seed);
+    norm2_kernel<<<1, kSpThreads, 0, st>>>(w.w, d, w.scal);
+    scale_kernel<<<grid_for(d), kSpThreads, 0, st>>>(w.w, d, w.scal, w.V, w.vf);
     count_launch(3);
     if (cudaGetLastError() != cudaSuccess) return RK_ECUDA;
 
@@ -333,22 +346,31 @@ int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint6
     std::vector<double> alpha, beta(1, 0.0);   // beta[j] couples steps j-1 and j
     double fro2 = 0.0;
     for (int j = 0; j < k; ++j) {
-        // w = A^T A v_j
         int rc = RK_EINVAL;
-        if (one_pass) {
-            rc = one_pass_normal_matvec(pl, w, n, st);
-            if (rc == RK_EINVAL) one_pass = false;   // rows too long for the solve kernel
+        if (wide) {
+            // w = A A^T v_j: y = -A^T v_j (n doubles, in w), its float32 copy, then -A y
+            rc = launch_transpose_matvec(A, m, n, lda, w.V + (size_t)j * (size_t)w.ldv, w.w, w.res, st);
+            if (rc != RK_OK) return rc;
+            to_float_kernel<<<grid_for(n), kSpThreads, 0, st>>>(w.w, n, w.vout);
+            count_launch();
+            rc = launch_rows_matvec(A, m, n, lda, w.vout, w.w, w.res, st);
+        } else {
+            // w = A^T A v_j
+            if (one_pass) {
+                rc = one_pass_normal_matvec(pl, w, n, st);
+                if (rc == RK_EINVAL) one_pass = false;   // rows too long for the solve kernel
+            }
+            if (!one_pass) rc = launch_normal_matvec(A, m, n, lda, w.vf, w.w, w.res, st);
         }
-        if (!one_pass) rc = launch_normal_matvec(A, m, n, lda, w.vf, w.w, w.res, st);
         if (rc != RK_OK) return rc;
         // two passes of classical Gram-Schmidt against v_0 .. v_j
         const int cnt = j + 1;
-        multi_dot_kernel<<<cnt, kSpThreads, 0, st>>>(w.V, w.ldv, w.w, n, w.c1);
-        multi_sub_kernel<<<grid_for(n), kSpThreads, 0, st>>>(w.w, w.V, w.ldv, cnt, w.c1, n);
-        multi_dot_kernel<<<cnt, kSpThreads, 0, st>>>(w.V, w.ldv, w.w, n, w.c2);
-        multi_sub_kernel<<<grid_for(n), kSpThreads, 0, st>>>(w.w, w.V, w.ldv, cnt, w.c2, n);
-        norm2_kernel<<<1, kSpThreads, 0, st>>>(w.w, n, w.scal);
-        scale_kernel<<<grid_for(n), kSpThreads, 0, st>>>(w.w, n, w.scal, w.V + (size_t)cnt * (size_t)w.ldv,
+        multi_dot_kernel<<<cnt, kSpThreads, 0, st>>>(w.V, w.ldv, w.w, d, w.c1);
+        multi_sub_kernel<<<grid_for(d), kSpThreads, 0, st>>>(w.w, w.V, w.ldv, cnt, w.c1, d);
+        multi_dot_kernel<<<cnt, kSpThreads, 0, st>>>(w.V, w.ldv, w.w, d, w.c2);
+        multi_sub_kernel<<<grid_for(d), kSpThreads, 0, st>>>(w.w, w.V, w.ldv, cnt, w.c2, d);
+        norm2_kernel<<<1, kSpThreads, 0, st>>>(w.w, d, w.scal);
+        scale_kernel<<<grid_for(d), kSpThreads, 0, st>>>(w.w, d, w.scal, w.V + (size_t)cnt * (size_t)w.ldv,
                                                          w.vf);
         count_launch(6);
         double h[4];
@@ -356,8 +378,8 @@ int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint6
         if (cudaMemcpyAsync(&h[0], w.c1 + j, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(&h[1], w.c2 + j, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(&h[2], w.scal, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            (one_pass && cudaMemcpyAsync(&solve_status, w.solve, sizeof(int), cudaMemcpyDeviceToHost,
-                                         st) != cudaSuccess) ||
+            (!wide && one_pass && cudaMemcpyAsync(&solve_status, w.solve, sizeof(int),
+                                                  cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return RK_ECUDA;
         if (solve_status != 0) return solve_status;
@@ -366,10 +388,10 @@ int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint6
         alpha.push_back(h[0] + h[1]);   // <A^T A v_j, v_j> with the second pass's correction
         const double bn = std::sqrt(h[2]);
         if (steps_done) *steps_done = j + 1;
-        // an invariant subspace ends the process (always by j = n - 1)
+        // an invariant subspace ends the process (always by j = d - 1)
         double amax = 0.0;
         for (double a : alpha) amax = std::fmax(amax, std::fabs(a));
-        if (!(bn > 1e-13 * amax) || j + 1 == n) break;
+        if (!(bn > 1e-13 * amax) || j + 1 == d) break;
         beta.push_back(bn);
     }
     beta.resize(alpha.size(), 0.0);

@@ -1,5 +1,6 @@
-"""Spectrum estimate (rk_spectrum: Lanczos on A^T A) against the oracle's FP64 SVD, and
-RKA with the optimal uniform weight of Eq. (best_alpha) against the oracle."""
+"""Spectrum estimate (rk_spectrum: Lanczos on A^T A) against the oracle's FP64 SVD, RKA
+with the optimal uniform weight of Eq. (best_alpha), and the Partial Matrix alpha of
+Section 3.3.1 (per-worker weights from each worker's row block) against the oracle."""
 import numpy as np
 import pytest
 
@@ -94,8 +95,8 @@ def test_rka_optimal_weight_reaches_tolerance_faster(rk):
 
 
 def test_spectrum_long_rows_two_pass(rk):
-    """Rows longer than the solve kernel holds (30000 columns) take the two residual
-    passes for A^T A v; the top of the spectrum still converges."""
+    """A wide matrix with rows longer than the solve kernel holds (30000 columns): the
+    process runs on A A^T (two passes a step); the top of the spectrum converges."""
     s = rk_inputs.gaussian_system(800, 30000, seed=4)
     A = _dev(s.A)
     sp = rk.spectrum(A, k=40, seed=1)
@@ -103,4 +104,97 @@ def test_spectrum_long_rows_two_pass(rk):
     ev = np.linalg.eigvalsh(s.A.astype(np.float64) @ s.A.T.astype(np.float64))
     assert sp.lambda_max == pytest.approx(ev[-1], rel=2e-3)
     assert sp.lambda_max <= ev[-1] * (1 + 1e-9)   # a Ritz value, from below
+    # the process runs on A A^T: the smallest Ritz value bounds the smallest nonzero
+    # eigenvalue from above, far from the 29200 zero eigenvalues of A^T A
+    assert sp.lambda_min >= ev[0] * (1 - 1e-6)
     assert sp.fro2 == pytest.approx(float(np.sum(s.A.astype(np.float64) ** 2)), rel=1e-12)
+
+
+def test_spectrum_wide_spanning_row_space(rk):
+    """m < n with k = m steps (Lanczos on A A^T spans R^m): the end Ritz values are the
+    extreme squared singular values (the oracle's SVD of a 60 x 400 A)."""
+    rng = np.random.default_rng(6)
+    A_np = rng.standard_normal((60, 400)).astype(np.float32)
+    lmin, lmax, fro2 = oracle.spectrum(A_np)
+    sp = rk.spectrum(_dev(A_np), k=200, seed=2)
+    assert sp.steps == 60
+    assert sp.lambda_min == pytest.approx(lmin, rel=1e-5)
+    assert sp.lambda_max == pytest.approx(lmax, rel=1e-5)
+
+
+@pytest.mark.parametrize("m,n,q", [(1200, 40, 4), (1200, 40, 40), (999, 64, 7)])
+def test_partial_alpha_matches_oracle(rk, m, n, q):
+    """Per-worker alpha of Section 3.3.1 from each block (tall blocks, wide blocks of 30 x
+    40, ragged blocks of 142 or 143 rows) with enough Lanczos steps to span each block's
+    row space, against the oracle's (LAPACK SVD of every block).  The float32 application
+    of A^T A errs by about 1e-7 lambda_max, so lambda_min of an ill-conditioned block is
+    held to 1e-3 and the weights (which depend on it through (q - 1) s_min) to 1e-4."""
+    s = rk_inputs.gaussian_system(m, n, seed=m + q)
+    w, sps = rk.partial_alpha_star(rk.aligned_rows(_dev(s.A)), q, k=min(n, 512))
+    w_o, sp_o = oracle.partial_alpha_star(s.A, q)
+    np.testing.assert_allclose(w.cpu().numpy(), w_o, rtol=1e-4)
+    for g in range(q):
+        assert sps[g].lambda_min == pytest.approx(sp_o[g, 0], rel=1e-3)
+        assert sps[g].lambda_max == pytest.approx(sp_o[g, 1], rel=1e-5)
+        assert sps[g].fro2 == pytest.approx(sp_o[g, 2], rel=1e-12)
+
+
+def test_partial_alpha_refuses_empty_blocks(rk):
+    A = torch.randn((10, 8), device="cuda")
+    with pytest.raises(rk.RkError):
+        rk.partial_alpha_star(A, 11)
+
+
+@pytest.mark.parametrize("q,alpha,rounds,sampling,cluster", [
+    (8, 20, 6, "full", 0),        # one CTA a worker
+    (8, 20, 6, "blocks", 0),      # the Distributed Approach
+    (456, 1, 12, "full", 0),      # RKA with more workers than SMs (workers spread over CTAs)
+    (456, 1, 12, "blocks", 0),
+    (4, 20, 5, "full", 4),        # 4-CTA cluster workers
+])
+def test_worker_weights_match_oracle(rk, q, alpha, rounds, sampling, cluster):
+    """Per-worker weights (here the Partial Matrix alpha, scaled into (0.5, 1.5) of a
+    uniform relaxation so that every worker's weight differs): x within 1e-4 of the oracle
+    given the same weights."""
+    s = rk_inputs.gaussian_system(2000, 100, seed=0)
+    tab = oracle.table(s.A)
+    u = np.float32(0.5) + np.random.default_rng(q).random(q).astype(np.float32)
+    plan = rk.rk_setup(rk.aligned_rows(_dev(s.A)))
+    x, info = rk.rkab_solve(plan, _dev(s.b), q=q, alpha=alpha, rounds=rounds, seed=3,
+                            check_every=0, sampling=sampling, cluster_size=cluster,
+                            worker_weight=_dev(u))
+    assert info.status == 0
+    x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=q, alpha=alpha,
+                      rounds=rounds, seed=3, tab=tab, sampling=sampling,
+                      worker_weight=u.astype(np.float64))
+    err = np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o)
+    assert err < 1e-4
+
+
+@pytest.mark.parametrize("q,sampling", [(4, "full"), (16, "blocks")])
+def test_partial_alpha_rka_matches_oracle(rk, q, sampling):
+    """RKA with the Partial Matrix alpha end to end: the GPU's weights (rk_partial_alpha_star,
+    k spanning each block) and the oracle's own weights (SVD) drive the two solves; x
+    within 1e-4, and the run reaches 1e-6 in about the rounds of the full-matrix alpha*
+    (Table 1)."""
+    s = rk_inputs.gaussian_system(4000, 60, seed=21)
+    tab = oracle.table(s.A)
+    A = rk.aligned_rows(_dev(s.A))
+    w, _ = rk.partial_alpha_star(A, q, k=60)
+    w_o, _ = oracle.partial_alpha_star(s.A, q)
+    plan = rk.rk_setup(A)
+    x, info = rk.rka_solve(plan, _dev(s.b), q=q, rounds=50, seed=7, check_every=0,
+                           sampling=sampling, worker_weight=w)
+    assert info.status == 0
+    x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(60), q=q, alpha=1, rounds=50,
+                      seed=7, tab=tab, sampling=sampling, worker_weight=w_o)
+    assert np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o) < 1e-4
+    xs = _dev(s.x_star)
+    lmin, lmax, fro2 = oracle.spectrum(s.A)
+    a = oracle.alpha_star(q, lmin / fro2, lmax / fro2)
+    _, i_full = rk.rka_solve(plan, _dev(s.b), q=q, rounds=100000, seed=1, omega=a, tol=1e-6,
+                             x_ref=xs, sampling=sampling)
+    _, i_part = rk.rka_solve(plan, _dev(s.b), q=q, rounds=100000, seed=1, tol=1e-6, x_ref=xs,
+                             sampling=sampling, worker_weight=w)
+    assert i_full.last_metric < 1e-6 and i_part.last_metric < 1e-6
+    assert abs(i_part.rounds_done - i_full.rounds_done) <= 0.1 * i_full.rounds_done
