@@ -98,31 +98,45 @@ __global__ void scale_kernel(const double* __restrict__ w, int64_t n, const doub
     }
 }
 
-// Per-block partial sums of a_ij^2: one warp per row, each lane accumulating the
-// exact squares (a a = p + e, e = fma(a, a, -p)) in a compensated float32 pair
-// (TwoSum; about 2^-46 relative), the pairs combined in FP64 per block.  The
-// FP64 pipe of the device is slow, so no FP64 operation runs per element.
+// a^2 added to the compensated float32 pair (hi, lo): a a = p + e exactly
+// (e = fma(a, a, -p)), p by TwoSum.
+__device__ __forceinline__ void add_square(float& hi, float& lo, float t) {
+    const float p = __fmul_rn(t, t);
+    const float e = fmaf(t, t, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// Per-block partial sums of a_ij^2: one warp per row, each lane reading float4
+// slices (four in flight) and accumulating the exact squares in two compensated
+// float32 pairs (TwoSum; about 2^-46 relative), the pairs combined in FP64 per
+// block.  The FP64 pipe of the device is slow, so no FP64 operation runs per
+// element.  Rows are 16-byte aligned (lda a multiple of 4).
 __global__ void __launch_bounds__(kSpThreads) fro_rows_kernel(const float* __restrict__ A, int64_t m,
                                                               int64_t n, int64_t lda,
                                                               double* __restrict__ part) {
     __shared__ double sh[kSpThreads];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float hi = 0.f, lo = 0.f;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    const int64_t n4 = n / 4;
     for (int64_t i = (int64_t)blockIdx.x * (kSpThreads / 32) + warp; i < m;
          i += (int64_t)gridDim.x * (kSpThreads / 32)) {
         const float* a = A + i * lda;
-        for (int64_t j = lane; j < n; j += 32) {
-            const float t = __ldcs(a + j);
-            const float p = __fmul_rn(t, t);
-            const float e = fmaf(t, t, -p);
-            const float s = __fadd_rn(hi, p);
-            const float bb = __fsub_rn(s, hi);
-            const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-            hi = s;
-            lo = __fadd_rn(lo, __fadd_rn(err, e));
+        const float4* a4 = reinterpret_cast<const float4*>(a);
+#pragma unroll 4
+        for (int64_t c = lane; c < n4; c += 32) {
+            const float4 v = __ldcs(a4 + c);
+            add_square(h0, l0, v.x);
+            add_square(h1, l1, v.y);
+            add_square(h0, l0, v.z);
+            add_square(h1, l1, v.w);
         }
+        for (int64_t j = n4 * 4 + lane; j < n; j += 32) add_square(h0, l0, __ldcs(a + j));
     }
-    const double s = block_sum((double)hi + (double)lo, sh);
+    const double s = block_sum(((double)h0 + (double)l0) + ((double)h1 + (double)l1), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
