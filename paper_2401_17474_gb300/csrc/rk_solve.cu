@@ -25,18 +25,13 @@ __global__ void sample_indices_kernel(const uint64_t* __restrict__ thr64,
 
 // Consumer threads per CTA: few warps keep the per-projection reduction short,
 // enough slices per thread keep the FMA pipe busy, and the register file bounds
-// x, d and the row slices (256 consumers + 1 producer warp may use 170
+// x, d and the row slices (256 consumers + 1 producer warp may use 168
 // registers/thread, 512 + 1 only 96): 32 threads up to n = 512, 128 up to
-// n = 2560, 256 up to n = 10240, else 512 (row re-read from shared memory);
-// then the smallest instantiated slices-per-thread count that covers n.
-static const SolveVariant* pick_variant(rk_dtype dt, int n4, int w, int minb = 1, bool jac = false) {
-    int count = 0;
-    const SolveVariant* tab = dt == RK_F32 ? solve_variants_f32(&count)
-                            : dt == RK_BF16 ? solve_variants_bf16(&count)
-                                            : solve_variants_fp8(&count);
-    int nt = n4 <= 32 * 4 ? 32 : (n4 <= 128 * 5 ? 128 : (n4 <= 256 * 10 ? 256 : 512));
-    // two workers per SM: 128 or 256 consumers, slices re-read from shared memory
-    if (minb == 2) nt = n4 <= 128 * 5 ? 128 : 256;
+// n = 2560, 256 up to n = 16384 (beyond 10240 columns with the row re-read from
+// shared memory: half the warps of a 512-thread CTA to reduce each dot over), else
+// 512; then the smallest instantiated slices-per-thread count that covers n.
+static const SolveVariant* find_variant(const SolveVariant* tab, int count, int nt, int n4, int w,
+                                        int minb, bool jac) {
     const int need = (n4 + nt - 1) / nt;
     const SolveVariant* best = nullptr;
     for (int i = 0; i < count; ++i) {
@@ -45,6 +40,21 @@ static const SolveVariant* pick_variant(rk_dtype dt, int n4, int w, int minb = 1
             best = &tab[i];
     }
     return best;
+}
+
+static const SolveVariant* pick_variant(rk_dtype dt, int n4, int w, int minb = 1, bool jac = false) {
+    int count = 0;
+    const SolveVariant* tab = dt == RK_F32 ? solve_variants_f32(&count)
+                            : dt == RK_BF16 ? solve_variants_bf16(&count)
+                                            : solve_variants_fp8(&count);
+    int nt = n4 <= 32 * 4 ? 32 : (n4 <= 128 * 5 ? 128 : (n4 <= 256 * 10 ? 256 : 512));
+    // two workers per SM: 128 or 256 consumers, slices re-read from shared memory
+    if (minb == 2) nt = n4 <= 128 * 5 ? 128 : 256;
+    if (nt == 512 && n4 <= 256 * 16) {
+        const SolveVariant* v = find_variant(tab, count, 256, n4, w, minb, jac);
+        if (v) return v;
+    }
+    return find_variant(tab, count, nt, n4, w, minb, jac);
 }
 
 static const int kMaxStages = 16;

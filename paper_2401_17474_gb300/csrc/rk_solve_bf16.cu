@@ -12,6 +12,7 @@ static const SolveVariant kTab[] = {
     V_(256, 3, true, 1),   V_(256, 4, true, 1),   V_(256, 5, true, 1),   V_(256, 6, true, 1),
     V_(256, 8, true, 1),   V_(256, 10, true, 1),
     V_(512, 6, false, 1),  V_(512, 8, false, 1),  V_(512, 10, false, 1),
+    V_(256, 12, false, 1), V_(256, 16, false, 1),
     V_(128, 2, false, 2),  V_(128, 3, false, 2),  V_(128, 5, false, 2),
     V_(256, 3, false, 2),  V_(256, 4, false, 2),  V_(256, 5, false, 2),  V_(256, 6, false, 2),
     V_(256, 8, false, 2),  V_(256, 10, false, 2),

@@ -164,7 +164,9 @@ def test_c1_rk_and_rka_match_oracle(rk, c1, q, k):
     (3001, 37, 3, 7, 20, 1.0),       # ragged n (tail of a float4), several stages
     (5000, 300, 8, 50, 6, 1.5),      # relaxation
     (4000, 1000, 16, 40, 4, 1.0),    # 128-thread CTAs, wider rows
-    (6000, 2600, 5, 30, 3, 0.8),     # 512-thread CTAs
+    (6000, 2600, 5, 30, 3, 0.8),     # 256-thread CTAs, 3 slices a thread
+    (3000, 12000, 3, 20, 2, 1.0),    # 256-thread CTAs, 12 slices a thread, row re-read from shared memory
+    (2000, 15003, 2, 15, 2, 1.2),    # 16 slices a thread, ragged tail
     (800, 5, 2, 3, 50, 1.0),         # n < 8
 ])
 def test_rkab_matches_oracle(rk, m, n, q, alpha, rounds, omega):
