@@ -410,6 +410,13 @@ size_t rk_spectrum_workspace_bytes(int64_t m, int64_t n, int k);
 int rk_spectrum(const float *A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed,
                 void *workspace, size_t ws_bytes, void *stream, double *out, int *steps_done);
 
+/* rk_spectrum with ||A||_F^2 supplied by the caller (fro2 > 0), skipping its pass over A:
+ * out[2] <- fro2.  A plan of A gives it as T 2^L (rk_plan_status), its exact-integer
+ * sampling law, to about 1e-8 relative.  fro2 <= 0 computes it like rk_spectrum. */
+int rk_spectrum_ex(const float *A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed,
+                   double fro2, void *workspace, size_t ws_bytes, void *stream, double *out,
+                   int *steps_done);
+
 /* Bytes of device workspace rk_partial_alpha_star needs. */
 size_t rk_partial_alpha_workspace_bytes(int64_t m, int64_t n, int q, int k);
 

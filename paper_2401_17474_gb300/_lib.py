@@ -107,6 +107,9 @@ _SIG = {
     "rk_spectrum": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                    ctypes.c_uint64, _V, ctypes.c_size_t, _V,
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "rk_spectrum_ex": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                      ctypes.c_uint64, ctypes.c_double, _V, ctypes.c_size_t, _V,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "rk_partial_alpha_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                                            ctypes.c_int]),
     "rk_partial_alpha_star": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,

@@ -7,6 +7,7 @@ Workspaces are allocated here with torch (the library never allocates).
 from __future__ import annotations
 
 import ctypes
+import math
 from dataclasses import dataclass
 
 import torch
@@ -87,6 +88,12 @@ class Plan:
         check(_lib.load().rk_plan_status(self._h, _stream(stream), ctypes.byref(T),
                                          ctypes.byref(Lx)), "rk_plan_status")
         return int(T.value), int(Lx.value)
+
+    def frobenius2(self, stream=None) -> float:
+        """||A||_F^2 of the stored rows from the exact-integer law: T 2^L (each row weight
+        truncated to the law's bits; about 1e-8 relative).  Synchronises."""
+        T, L = self.status(stream)
+        return math.ldexp(float(T), L)
 
     def tables(self):
         """Device tensors K (int64 view of uint64), P, thr64, alias (int32 view), inv."""
@@ -383,8 +390,9 @@ class Spectrum:
         return self.lambda_max / self.fro2
 
 
-def spectrum(A: torch.Tensor, k: int = 32, seed: int = 0, stream=None) -> Spectrum:
-    """Extreme eigenvalues of A^T A and ||A||_F^2 by k Lanczos steps (rk_spectrum)."""
+def spectrum(A: torch.Tensor, k: int = 32, seed: int = 0, stream=None, fro2=None) -> Spectrum:
+    """Extreme squared singular values of A by k Lanczos steps, and ||A||_F^2 (rk_spectrum;
+    rk_spectrum_ex with a known ||A||_F^2, e.g. `Plan.frobenius2()`, skips that pass)."""
     if A.dtype != torch.float32 or A.stride(1) != 1 or not A.is_cuda:
         raise ValueError("A must be a float32 CUDA matrix with unit column stride")
     m, n = A.shape
@@ -395,14 +403,19 @@ def spectrum(A: torch.Tensor, k: int = 32, seed: int = 0, stream=None) -> Spectr
     ws = _workspace(nbytes, A.device)
     out = (ctypes.c_double * 3)()
     steps = ctypes.c_int(0)
-    check(lib.rk_spectrum(_ptr(A), m, n, A.stride(0), int(k), int(seed), _ptr(ws), ws.numel(),
-                          _stream(stream), out, ctypes.byref(steps)), "rk_spectrum")
+    if fro2 is None:
+        check(lib.rk_spectrum(_ptr(A), m, n, A.stride(0), int(k), int(seed), _ptr(ws), ws.numel(),
+                              _stream(stream), out, ctypes.byref(steps)), "rk_spectrum")
+    else:
+        check(lib.rk_spectrum_ex(_ptr(A), m, n, A.stride(0), int(k), int(seed), float(fro2), _ptr(ws),
+                                 ws.numel(), _stream(stream), out, ctypes.byref(steps)), "rk_spectrum_ex")
     return Spectrum(out[0], out[1], out[2], steps.value)
 
 
-def optimal_weight(A: torch.Tensor, q: int, k: int = 32, seed: int = 0, stream=None):
-    """(alpha*, Spectrum): the weight of Eq. (best_alpha) for RKA with q workers on A."""
-    sp = spectrum(A, k, seed, stream)
+def optimal_weight(A: torch.Tensor, q: int, k: int = 32, seed: int = 0, stream=None, plan=None):
+    """(alpha*, Spectrum): the weight of Eq. (best_alpha) for RKA with q workers on A; with
+    the plan of A, ||A||_F^2 comes from its sampling law instead of a pass over A."""
+    sp = spectrum(A, k, seed, stream, None if plan is None else plan.frobenius2())
     return alpha_star(q, sp.s_min, sp.s_max), sp
 
 

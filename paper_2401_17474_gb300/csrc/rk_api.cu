@@ -485,6 +485,17 @@ int rk_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint64
                         steps_done);
 }
 
+int rk_spectrum_ex(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed, double fro2,
+                   void* workspace, size_t ws_bytes, void* stream, double* out, int* steps_done) {
+    if (!A || !workspace || !out || m < 1 || n < 1 || lda < n || k < 1 || k > 512) return RK_EINVAL;
+    if (!aligned16(A) || (lda * 4) % 16 != 0 || ((uintptr_t)workspace & 255u) != 0) return RK_EALIGN;
+    if (!std::isfinite(fro2)) return RK_EINVAL;
+    const int kk = lanczos_steps(m, n, k);
+    if (ws_bytes < spectrum_ws_bytes(m, n, kk)) return RK_EWORKSPACE;
+    return run_spectrum(A, m, n, lda, kk, seed, workspace, static_cast<cudaStream_t>(stream), out,
+                        steps_done, fro2);
+}
+
 size_t rk_partial_alpha_workspace_bytes(int64_t m, int64_t n, int q, int k) {
     if (m < 1 || n < 1 || q < 1 || q > m || k < 1 || k > 512) return 0;
     const int64_t rows = (m + q - 1) / q + 1;   // the largest block

@@ -107,7 +107,7 @@ int launch_transpose_matvec(const float* A, int64_t m, int64_t n, int64_t lda, c
                             double* w, void* ws, cudaStream_t st);
 size_t spectrum_ws_bytes(int64_t m, int64_t n, int k);
 int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed, void* ws,
-                 cudaStream_t st, double* out, int* steps_done);
+                 cudaStream_t st, double* out, int* steps_done, double fro2_known = 0.0);
 
 int launch_quantize(const float* A, int64_t m, int64_t n, int64_t lda, rk_dtype dt, void* out,
                     int64_t ldo, float* row_scale, cudaStream_t st);

@@ -321,14 +321,16 @@ static int grid_for(int64_t n) {
 }
 
 int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed, void* ws,
-                 cudaStream_t st, double* out, int* steps_done) {
+                 cudaStream_t st, double* out, int* steps_done, double fro2_known) {
     SpecWs w = spec_carve(ws, m, n, k);
     if (steps_done) *steps_done = 0;
-    // ||A||_F^2
-    const int fb = fro_blocks(m);
-    fro_rows_kernel<<<fb, kSpThreads, 0, st>>>(A, m, n, lda, w.fpart);
-    sum_parts_kernel<<<1, 32, 0, st>>>(w.fpart, fb, w.scal + 1);
-    count_launch(2);
+    // ||A||_F^2, unless the caller knows it
+    if (!(fro2_known > 0.0)) {
+        const int fb = fro_blocks(m);
+        fro_rows_kernel<<<fb, kSpThreads, 0, st>>>(A, m, n, lda, w.fpart);
+        sum_parts_kernel<<<1, 32, 0, st>>>(w.fpart, fb, w.scal + 1);
+        count_launch(2);
+    }
     // the process runs on A^T A in R^n, or for m < n on A A^T in R^m: the same nonzero
     // eigenvalues without the n - m zero ones, which rounding would otherwise bring in
     // (a well separated end of the spectrum, found within a few steps)
@@ -410,7 +412,7 @@ int run_spectrum(const float* A, int64_t m, int64_t n, int64_t lda, int k, uint6
     }
     beta.resize(alpha.size(), 0.0);
     tridiag_extremes(alpha, beta, &out[0], &out[1]);
-    out[2] = fro2;
+    out[2] = fro2_known > 0.0 ? fro2_known : fro2;
     return RK_OK;
 }
 

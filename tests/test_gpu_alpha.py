@@ -198,3 +198,20 @@ def test_partial_alpha_rka_matches_oracle(rk, q, sampling):
                              sampling=sampling, worker_weight=w)
     assert i_full.last_metric < 1e-6 and i_part.last_metric < 1e-6
     assert abs(i_part.rounds_done - i_full.rounds_done) <= 0.1 * i_full.rounds_done
+
+
+def test_spectrum_with_known_frobenius_norm(rk):
+    """rk_spectrum_ex skips the Frobenius pass: the same Lanczos extremes as rk_spectrum,
+    ||A||_F^2 as given; the plan's law gives ||A||_F^2 = T 2^L within 1e-7 of the oracle's."""
+    s = rk_inputs.gaussian_system(3000, 200, seed=2)
+    A = _dev(s.A)
+    plan = rk.rk_setup(A)
+    fro2_o = oracle.spectrum(s.A)[2]
+    assert plan.frobenius2() == pytest.approx(fro2_o, rel=1e-7)
+    a = rk.spectrum(A, k=12, seed=5)
+    b = rk.spectrum(A, k=12, seed=5, fro2=plan.frobenius2())
+    assert (b.lambda_min, b.lambda_max) == (a.lambda_min, a.lambda_max)
+    assert b.fro2 == plan.frobenius2()
+    w_plan, _ = rk.optimal_weight(A, 64, k=12, seed=5, plan=plan)
+    w_pass, _ = rk.optimal_weight(A, 64, k=12, seed=5)
+    assert w_plan == pytest.approx(w_pass, rel=1e-6)
