@@ -668,6 +668,34 @@ def _cgls_ls(A, b, iters=40, tol=1e-12, rows=32768):
     return x
 
 
+def _refine_sweep(rk, A, b, x0, x, alpha, q, kind, x_ref, args):
+    """BF16 / FP8 stored rows + refinement on the FP32 master to ||x - x_ref||/||x_ref|| <
+    tol, timed alone (the stored copy and its plan built beforehand), for several inner
+    rounds per outer step (more rounds a step, fewer 64 GB residual passes); the fastest
+    schedule that reaches tol, with the whole sweep."""
+    import torch
+    Aq, sc = rk.quantize(A, kind)
+    lowp = rk.rk_setup(Aq, kind, sc)
+    ref = rk.Refiner(lowp, q)
+    oo = rk.make_opts(check_every=0, tol=args.tol, x_ref=x_ref)
+    sweep = {}
+    for inner in (4, 5, 6, 8):
+        holder = {}
+
+        def go():
+            holder["i"] = ref.run(A, b, x0, x, alpha, inner, 40, args.seed, oo)
+        t = _timed(go, reps=1)
+        sweep[f"inner{inner}"] = {"ms": round(t, 2), "outer": holder["i"].outer_done,
+                                  "metric": holder["i"].last_metric}
+    del Aq, lowp, ref
+    torch.cuda.empty_cache()
+    ok = [(v["ms"], k) for k, v in sweep.items() if 0 <= v["metric"] < args.tol]
+    best = min(ok)[1] if ok else min((v["metric"], k) for k, v in sweep.items())[1]
+    return dict(sweep[best], inner_rounds=int(best[5:]),
+                note="solve alone (stored copy and its plan built beforehand); fastest "
+                     "schedule of the sweep that reaches tol", sweep=sweep)
+
+
 def precision_inconsistent(rk, A, plan, b, n, q, alpha, args, dev):
     """The inconsistent variant: b + e, e ~ N(0, 1e-4^2); time to ||x - x_LS||/||x_LS|| < 1e-6
     for plain FP32 RKAB, BF16 / FP8 + refinement and RKA with alpha* (4864 workers), x_LS from
@@ -700,21 +728,9 @@ def precision_inconsistent(rk, A, plan, b, n, q, alpha, args, dev):
                                          "metric": sa.info().last_metric}
     for kind in ("bf16", "fp8"):
         try:
-            Aq, sc = rk.quantize(A, kind)
-            lowp = rk.rk_setup(Aq, kind, sc)
-            ref = rk.Refiner(lowp, q)
-            oo = rk.make_opts(check_every=0, tol=args.tol, x_ref=xr)
-            holder = {}
-
-            def go():
-                holder["i"] = ref.run(A, b_inc, x0, x, alpha, 4, 40, args.seed, oo)
-            t = _timed(go, reps=1)
-            out[f"{kind}_refine"] = {"ms": round(t, 2), "outer": holder["i"].outer_done,
-                                     "inner_rounds": 4, "metric": holder["i"].last_metric}
-            del Aq, lowp, ref
+            out[f"{kind}_refine"] = _refine_sweep(rk, A, b_inc, x0, x, alpha, q, kind, xr, args)
         except Exception as e:
             out[f"{kind}_refine"] = {"error": str(e)}
-        torch.cuda.empty_cache()
     return out
 
 
@@ -753,26 +769,17 @@ def run_precision(args, rk, dev):
     total = e0.elapsed_time(e1)
     inf = solver.info()
     units = q * alpha * inf.rounds_done * args.steps
-    out = {"fp32_plain": {"ms": round(total / args.steps, 2), "rounds": inf.rounds_done,
-                          "metric": inf.last_metric}}
+    # the solve alone (the plan built beforehand), as the stored-row runs below are timed
+    t_solve = _timed(lambda: solver.launch(b, x0, x, alpha, args.max_rounds, args.seed, o), reps=1)
+    out = {"fp32_plain": {"ms": round(total / args.steps, 2), "solve_ms": round(t_solve, 2),
+                          "rounds": inf.rounds_done, "metric": inf.last_metric,
+                          "note": "ms: setup + solve (the line's step); solve_ms: solve alone"}}
     sp = rk.spectrum(A, k=4)
     for kind in ("bf16", "fp8"):
         try:
-            Aq, sc = rk.quantize(A, kind)
-            lowp = rk.rk_setup(Aq, kind, sc)
-            ref = rk.Refiner(lowp, q)
-            oo = rk.make_opts(check_every=0, tol=args.tol, x_ref=xs)
-            holder = {}
-
-            def go():
-                holder["i"] = ref.run(A, b, x0, x, alpha, 4, 40, args.seed, oo)
-            t = _timed(go, reps=1)
-            out[f"{kind}_refine"] = {"ms": round(t, 2), "outer": holder["i"].outer_done,
-                                     "inner_rounds": 4, "metric": holder["i"].last_metric}
-            del Aq, lowp, ref
+            out[f"{kind}_refine"] = _refine_sweep(rk, A, b, x0, x, alpha, q, kind, xs, args)
         except Exception as e:
             out[f"{kind}_refine"] = {"error": str(e)}
-        torch.cuda.empty_cache()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     for qa in (sms, 32 * sms):
         s3 = rk.Solver(plan, qa)

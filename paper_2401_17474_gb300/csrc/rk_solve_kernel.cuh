@@ -789,31 +789,29 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
             const bool got = wait_parity(&full[s], ph, p.timeout_ns, status);
             const uint8_t* stg = stages + (size_t)s * p.stage_stride;
             const float4 mb = meta[s];   // b_i, 1/||A_i||^2, row scale
-            // four independent accumulators (one per element of a slice) keep the
-            // FMA pipe fed; they are combined in a fixed order
-            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+            // four independent accumulators (one per element of a slice, two packed
+            // pairs: one FFMA2 per two products) keep the FMA pipe fed; they are
+            // combined in a fixed order
+            float2 p01 = make_float2(0.f, 0.f), p23 = make_float2(0.f, 0.f);
             float4 a[KEEP_A ? VPT : 1];
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 const int idx = tid + k * NT;
                 const float4 ak = slice<ELT>(stg, idx, k, tail_k, rem);
                 if constexpr (KEEP_A) a[k] = ak;
-                p0 = fmaf(ak.x, v[k].x, p0);
-                p1 = fmaf(ak.y, v[k].y, p1);
-                p2 = fmaf(ak.z, v[k].z, p2);
-                p3 = fmaf(ak.w, v[k].w, p3);
+                const float2 alo = make_float2(ak.x, ak.y), ahi = make_float2(ak.z, ak.w);
+                p01 = __ffma2_rn(alo, make_float2(v[k].x, v[k].y), p01);
+                p23 = __ffma2_rn(ahi, make_float2(v[k].z, v[k].w), p23);
                 if (!jac) {
-                    p0 = fmaf(ak.x, d[k].x, p0);
-                    p1 = fmaf(ak.y, d[k].y, p1);
-                    p2 = fmaf(ak.z, d[k].z, p2);
-                    p3 = fmaf(ak.w, d[k].w, p3);
+                    p01 = __ffma2_rn(alo, make_float2(d[k].x, d[k].y), p01);
+                    p23 = __ffma2_rn(ahi, make_float2(d[k].z, d[k].w), p23);
                 }
             }
             if constexpr (KEEP_A) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
-            float part = (p0 + p1) + (p2 + p3);
+            float part = (p01.x + p01.y) + (p23.x + p23.y);
 #pragma unroll
             for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
             if (lane == 0) red[rp * kRedSlots * 32 + warp] = part;
@@ -829,6 +827,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
             rp ^= 1;
             // A_i = s_i q_i: <A_i, v> = s_i <q_i, v>, d += (scale s_i) q_i
             const float scale = p.omega * (mb.x - mb.z * dot) * mb.y * mb.z;
+            const float2 sc2 = make_float2(scale, scale);
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 float4 ak;
@@ -838,10 +837,9 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
                     const int idx = tid + k * NT;
                     ak = slice<ELT>(stg, idx, k, tail_k, rem);
                 }
-                d[k].x = fmaf(scale, ak.x, d[k].x);
-                d[k].y = fmaf(scale, ak.y, d[k].y);
-                d[k].z = fmaf(scale, ak.z, d[k].z);
-                d[k].w = fmaf(scale, ak.w, d[k].w);
+                const float2 dlo = __ffma2_rn(sc2, make_float2(ak.x, ak.y), make_float2(d[k].x, d[k].y));
+                const float2 dhi = __ffma2_rn(sc2, make_float2(ak.z, ak.w), make_float2(d[k].z, d[k].w));
+                d[k] = make_float4(dlo.x, dlo.y, dhi.x, dhi.y);
             }
             if constexpr (!KEEP_A) {
                 __syncwarp();

@@ -291,6 +291,17 @@ def test_full_size_sampled_parity(rk):
     x, info = rk.rkab_solve(plan, b, q=q, alpha=n, rounds=400, seed=0, x_ref=xs, tol=1e-6)
     assert info.status == 0 and info.last_metric < 1e-6, info
     assert _rel(x.cpu().numpy(), s.x_star.astype(np.float64)) < 1e-6
+    # the fastest configuration at full size: RKA with 4864 workers spread over the CTAs and
+    # the weight alpha* (from 2 Lanczos steps, ||A||_F^2 from the plan): two rounds against
+    # the oracle, then convergence to 1e-6
+    qa = 4864
+    w, _ = rk.optimal_weight(A, qa, k=2, plan=plan)
+    x, info = rk.rka_solve(plan, b, q=qa, rounds=2, seed=0, omega=w, check_every=0)
+    xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(n), q=qa, alpha=1, rounds=2, seed=0,
+                     tab=tab, omega=float(np.float32(w)), threads=8)
+    assert _rel(x.cpu().numpy(), xo) < TOL
+    x, info = rk.rka_solve(plan, b, q=qa, rounds=400, seed=0, omega=w, x_ref=xs, tol=1e-6)
+    assert info.status == 0 and info.last_metric < 1e-6 and info.rounds_done < 120, info
 
 
 def test_wait_limit_ends_the_solve_with_a_status(rk):
