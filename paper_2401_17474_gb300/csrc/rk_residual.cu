@@ -18,6 +18,7 @@ struct ResWs {
     float2* rs;        // m: r_i split into float32 (hi, lo) for the A^T r pass
     double* rr_part;   // per-block sums of r_i^2
     double* atr_part;  // [row chunks][n]
+    double* atr_bpart; // per-block sums of c_j^2 for ||A^T r||
     double* norms;     // [2] when the caller passes none
 };
 
@@ -196,30 +197,46 @@ __global__ void __launch_bounds__(kResThreads) residual_atr_kernel(
     if (j0 + 3 < n) out[3] = (double)h3 + (double)l3;
 }
 
-// One block: norms[0] = sqrt(sum of rr partials), norms[1] = ||A^T r|| from the chunk partials.
-__global__ void __launch_bounds__(kResThreads) residual_finish_kernel(
-    const double* __restrict__ rr_part, int nblocks, const double* __restrict__ atr_part, int chunks,
-    int64_t n, double* __restrict__ norms) {
+// Columns of A^T r over the grid: c_j = sum of the chunk partials of column j (chunks
+// in ascending order), and per block the sum of c_j^2 over its columns (a fixed tree).
+__global__ void __launch_bounds__(kResThreads) atr_norm_parts_kernel(const double* __restrict__ atr_part,
+                                                                     int chunks, int64_t n,
+                                                                     double* __restrict__ bpart) {
     __shared__ double s_part[kResThreads];
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < nblocks; ++k) s += rr_part[k];
-        norms[0] = sqrt(s);
-    }
-    if (!atr_part) return;
     double acc = 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += kResThreads) {
+    for (int64_t j = (int64_t)blockIdx.x * kResThreads + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * kResThreads) {
         double c = 0.0;
         for (int k = 0; k < chunks; ++k) c += atr_part[(size_t)k * (size_t)n + j];
         acc = fma(c, c, acc);
     }
     s_part[threadIdx.x] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < kResThreads; ++k) s += s_part[k];
-        norms[1] = sqrt(s);
+    for (int h = kResThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) s_part[threadIdx.x] += s_part[threadIdx.x + h];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) bpart[blockIdx.x] = s_part[0];
+}
+
+static int atr_norm_blocks(int64_t n) {
+    const int64_t g = (n + kResThreads - 1) / kResThreads;
+    return (int)(g < 512 ? g : 512);
+}
+
+// One thread: norms[0] = sqrt(sum of rr partials), norms[1] = ||A^T r|| from the block
+// partials of atr_norm_parts_kernel (both summed in block order).
+__global__ void residual_finish_kernel(const double* __restrict__ rr_part, int nblocks,
+                                       const double* __restrict__ atr_bpart, int nbp,
+                                       double* __restrict__ norms) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int k = 0; k < nblocks; ++k) s += rr_part[k];
+    norms[0] = sqrt(s);
+    if (!atr_bpart) return;
+    double t = 0.0;
+    for (int k = 0; k < nbp; ++k) t += atr_bpart[k];
+    norms[1] = sqrt(t);
 }
 
 static ResWs carve(void* base, int64_t m, int64_t n) {
@@ -234,12 +251,14 @@ static ResWs carve(void* base, int64_t m, int64_t n) {
     w.rr_part = reinterpret_cast<double*>(p);
     p += align256((size_t)res_blocks(m) * 8);
     w.atr_part = reinterpret_cast<double*>(p);
+    p += align256((size_t)atr_chunks(m, n) * (size_t)n * 8);
+    w.atr_bpart = reinterpret_cast<double*>(p);
     return w;
 }
 
 size_t residual_ws_bytes(int64_t m, int64_t n) {
     return 256 + 2 * align256((size_t)m * 8) + align256((size_t)res_blocks(m) * 8) +
-           align256((size_t)atr_chunks(m, n) * (size_t)n * 8);
+           align256((size_t)atr_chunks(m, n) * (size_t)n * 8) + align256((size_t)atr_norm_blocks(n) * 8);
 }
 
 int launch_residual(const float* A, int64_t m, int64_t n, int64_t lda, const float* b,
@@ -258,8 +277,12 @@ int launch_residual(const float* A, int64_t m, int64_t n, int64_t lda, const flo
         residual_atr_kernel<<<grid, kResThreads, 0, st>>>(A, m, n, lda, w.rs, chunks, w.atr_part);
         count_launch();
     }
-    residual_finish_kernel<<<1, kResThreads, 0, st>>>(w.rr_part, nb, want_atr ? w.atr_part : nullptr,
-                                                      chunks, n, norms);
+    const int nbp = atr_norm_blocks(n);
+    if (want_atr) {
+        atr_norm_parts_kernel<<<nbp, kResThreads, 0, st>>>(w.atr_part, chunks, n, w.atr_bpart);
+        count_launch();
+    }
+    residual_finish_kernel<<<1, 32, 0, st>>>(w.rr_part, nb, want_atr ? w.atr_bpart : nullptr, nbp, norms);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
 }
