@@ -33,6 +33,7 @@
  *   orc_fp8e4m3_rne     FP32 -> FP8 e4m3 (OCP "fn" variant) round-to-nearest-even,
  *                       saturating to +-448
  */
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -110,16 +111,22 @@ int orc_row_weights(const float *A, int64_t m, int64_t n, int64_t lda,
     u128 *R = (u128 *)malloc(sizeof(u128) * (size_t)m);
     int *e = (int *)malloc(sizeof(int) * (size_t)m);
     if (!R || !e) { free(R); free(e); return ORC_ENOMEM; }
-    int have = 0, H = 0;
+    /* rows are independent: they may be taken by several threads; H is their maximum */
+    int have = 0, bad = 0, H = INT_MIN;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(max : H) reduction(| : have, bad)
+#endif
     for (int64_t i = 0; i < m; ++i) {
         const float *a = A + i * lda;
         double amax = 0.0;
+        int finite = 1;
         for (int64_t j = 0; j < n; ++j) {
             double v = fabs((double)a[j]);
-            if (!isfinite(v)) { free(R); free(e); return ORC_EINVAL; }
-            if (v > amax) amax = v;
+            if (!isfinite(v)) finite = 0;
+            else if (v > amax) amax = v;
         }
         R[i] = 0; e[i] = 0;
+        if (!finite) { bad = 1; continue; }
         if (amax == 0.0) continue;
         int ei;
         frexp(amax, &ei);
@@ -130,9 +137,10 @@ int orc_row_weights(const float *A, int64_t m, int64_t n, int64_t lda,
             R[i] += (u128)floor(scaled);
         }
         int h = bitlen128(R[i]) + 2 * ei - 102;
-        if (!have || h > H) { H = h; have = 1; }
+        if (h > H) H = h;
+        have = 1;
     }
-    if (!have) { free(R); free(e); return ORC_EINVAL; }
+    if (bad || !have) { free(R); free(e); return ORC_EINVAL; }
     int L = H + ceil_log2_i64(m) - 62;
     uint64_t T = 0;
     for (int64_t i = 0; i < m; ++i) {

@@ -304,6 +304,29 @@ def test_full_size_sampled_parity(rk):
     assert info.status == 0 and info.last_metric < 1e-6 and info.rounds_done < 120, info
 
 
+@pytest.mark.slow
+def test_lsq_size_sampled_parity(rk):
+    """200000 x 20000 (16 GB) with rows scaled by 10^U(-2,2) and b = A x* + N(0, 1e-3^2),
+    the least-squares workload in the benchmark's launch configuration (q = 132, rows of
+    80 KB): bit-exact tables, one short round of every worker against the oracle, and the
+    residual norms at that x against the oracle's FP64 residual."""
+    m, n, q = 200000, 20000, 132
+    A, b, _ = rk_inputs.gaussian_system_torch(m, n, seed=0, noise=1e-3, row_scale_decades=2.0,
+                                              device="cuda")
+    A_np = A.cpu().numpy()
+    b_np = b.cpu().numpy()
+    plan, tab = _check_tables(rk, A_np, rk.rk_setup(A))
+    x, info = rk.rkab_solve(plan, b, q=q, alpha=3, rounds=1, seed=0, check_every=0)
+    assert info.status == 0
+    xo = oracle.rkab(A_np, b_np.astype(np.float64), np.zeros(n), q=q, alpha=3, rounds=1, seed=0,
+                     tab=tab, threads=8)
+    assert _rel(x.cpu().numpy(), xo) < TOL
+    _, norms = rk.rk_residual(A, b, x)
+    _, rn, an = oracle.residual(A_np, b_np, x.cpu().numpy().astype(np.float64))
+    nn = norms.cpu().numpy()
+    assert abs(nn[0] - rn) <= 1e-12 * rn and abs(nn[1] - an) <= 1e-10 * an
+
+
 def test_wait_limit_ends_the_solve_with_a_status(rk):
     """Every device-side wait is bounded: with a 1 us limit the first wait for a row
     (a cold HBM copy takes longer) runs out, the kernel winds down (copies in flight
