@@ -222,14 +222,18 @@ def oracle_sample(A_np, b_np, tab, q, alpha_sample, seed, threads):
 
 
 def sample_alpha(A_np, b_np, tab, q, seed, threads, target_s):
-    """Projections per worker so that one oracle round takes about target_s:
-    two probes separate the fixed cost of a call (row norms) from the
-    per-projection cost."""
-    _, t1 = oracle_sample(A_np, b_np, tab, q, 10, seed, threads)
-    _, t2 = oracle_sample(A_np, b_np, tab, q, 40, seed, threads)
-    per = max((t2 - t1) / 30.0, 1e-7)
-    fixed = max(t1 - 10 * per, 0.0)
-    return max(10, int((target_s - fixed) / per))
+    """Projections per worker so that one oracle round takes about target_s: a first
+    probe warms the call up (pages of A, the thread pool) and is discarded; two warm
+    probes (40 and 200 projections a worker) separate the call's fixed cost (row norms)
+    from the cost of a projection, which is bounded below by a twentieth of the larger
+    probe's average so that a noisy difference cannot ask for an unbounded sample."""
+    oracle_sample(A_np, b_np, tab, q, 10, seed, threads)
+    _, t1 = oracle_sample(A_np, b_np, tab, q, 40, seed, threads)
+    _, t2 = oracle_sample(A_np, b_np, tab, q, 200, seed, threads)
+    avg = t2 / 200.0
+    per = max((t2 - t1) / 160.0, avg / 20.0, 1e-7)
+    fixed = max(t1 - 40.0 * per, 0.0)
+    return max(10, int(max(target_s - fixed, per) / per))
 
 
 def cpu_model():
