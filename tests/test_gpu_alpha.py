@@ -215,3 +215,15 @@ def test_spectrum_with_known_frobenius_norm(rk):
     w_plan, _ = rk.optimal_weight(A, 64, k=12, seed=5, plan=plan)
     w_pass, _ = rk.optimal_weight(A, 64, k=12, seed=5)
     assert w_plan == pytest.approx(w_pass, rel=1e-6)
+
+
+def test_new_entry_points_refuse_bad_arguments(rk):
+    """A non-finite ||A||_F^2 is refused by rk_spectrum_ex; per-worker weights must hold
+    exactly q floats."""
+    s = rk_inputs.gaussian_system(500, 40, seed=2)
+    A = _dev(s.A)
+    with pytest.raises(rk.RkError):
+        rk.spectrum(A, k=4, fro2=float("nan"))
+    plan = rk.rk_setup(A)
+    with pytest.raises(ValueError):
+        rk.rkab_solve(plan, _dev(s.b), q=4, alpha=2, rounds=1, worker_weight=_dev(np.ones(3, np.float32)))
