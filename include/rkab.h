@@ -279,7 +279,10 @@ size_t rk_refine_workspace_bytes(const rk_plan *lowp, int q);
  *       opts->omega
  *   x = x + d                   (float32)
  * and stops after max_outer steps or, with opts->criterion = 1, after the first step with
- * ||x - x_ref|| / ||x_ref|| < opts->tol.  Synchronises `stream` once per outer step to read
+ * ||x - x_ref|| / ||x_ref|| < opts->tol; with that criterion and tol > 0 each inner solve also
+ * checks x + d after every round and stops as soon as it meets the criterion (its reference is
+ * x_ref - x, its tolerance tol ||x_ref|| / ||x_ref - x||), so the rounds to tolerance are
+ * counted as for a plain solve.  Synchronises `stream` once per outer step to read
  * the inner solve's status and the criterion; returns RK_OK or the first error (device
  * status of an inner solve included).  *outer_done and *last_metric (may be NULL) receive
  * the steps done and the criterion after the last one (-1 without a criterion).

@@ -128,6 +128,7 @@ struct RefineWs {
     float* r32;
     float* d;
     float* zero;
+    float* cref;   // x_ref - x: the correction that meets the criterion exactly
     void* res_ws;
     size_t res_bytes;
     void* solve_ws;
@@ -148,6 +149,8 @@ static RefineWs refine_carve(void* base, const Plan* pl, int q) {
     p += align256(ldv * 4);
     w.zero = reinterpret_cast<float*>(p);
     p += align256(ldv * 4);
+    w.cref = reinterpret_cast<float*>(p);
+    p += align256(ldv * 4);
     w.res_ws = p;
     w.res_bytes = align256(residual_ws_bytes(pl->m, pl->n));
     p += w.res_bytes;
@@ -158,8 +161,16 @@ static RefineWs refine_carve(void* base, const Plan* pl, int q) {
 
 size_t refine_ws_bytes(const Plan* pl, int q) {
     const size_t ldv = (size_t)((pl->n + 3) / 4) * 4;
-    return 256 + align256((size_t)pl->m * 8) + align256((size_t)pl->m * 4) + 2 * align256(ldv * 4) +
+    return 256 + align256((size_t)pl->m * 8) + align256((size_t)pl->m * 4) + 3 * align256(ldv * 4) +
            align256(residual_ws_bytes(pl->m, pl->n)) + solve_ws_bytes(pl, q);
+}
+
+// c = x_ref - x (float32)
+__global__ void sub_kernel(const float* __restrict__ xr, const float* __restrict__ x, int64_t n,
+                           float* __restrict__ c) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        c[j] = xr[j] - x[j];
 }
 
 int run_refine(const Plan* lowp, const float* A32, int64_t lda32, const float* b, const float* x0,
@@ -174,6 +185,20 @@ int run_refine(const Plan* lowp, const float* A32, int64_t lda32, const float* b
         return RK_ECUDA;
     if (cudaMemsetAsync(w.zero, 0, (size_t)n * 4, st) != cudaSuccess) return RK_ECUDA;
     const int g = qgrid((m + 255) / 256 + 1);
+    const int gn = qgrid((n + 255) / 256 + 1);
+    // with a reference solution and a tolerance, every inner solve also stops as soon as
+    // x + d meets the criterion: its reference is c = x_ref - x and its tolerance
+    // tol ||x_ref|| / ||c|| (||x + d - x_ref|| = ||d - c||); err0 holds ||x - x_ref||^2 and
+    // ||x_ref||^2 of the current x
+    const bool exact_stop = o.criterion == 1 && o.x_ref && o.tol > 0.0;
+    double err0[2] = {0.0, 0.0};
+    if (exact_stop) {
+        relerr_kernel<<<1, kQThreads, 0, st>>>(x, o.x_ref, n, w.err);
+        count_launch();
+        if (cudaMemcpyAsync(err0, w.err, sizeof(err0), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return RK_ECUDA;
+    }
     for (int64_t outer = 0; outer < max_outer; ++outer) {
         int rc = launch_residual(A32, m, n, lda32, b, x, w.r64, nullptr, 0, w.res_ws, st);
         if (rc != RK_OK) return rc;
@@ -198,6 +223,14 @@ int run_refine(const Plan* lowp, const float* A32, int64_t lda32, const float* b
         io.sampling = o.sampling;
         io.row_weight = o.row_weight;
         io.worker_weight = o.worker_weight;
+        if (exact_stop && err0[0] > 0.0) {
+            sub_kernel<<<gn, 256, 0, st>>>(o.x_ref, x, n, w.cref);
+            count_launch();
+            io.criterion = 1;
+            io.x_ref = w.cref;
+            io.check_every = 1;
+            io.tol = o.tol * std::sqrt(err0[1] / err0[0]);
+        }
         a.opts = io;
         a.info = static_cast<SolveInfo*>(w.solve_ws);
         a.ldv = (n + 3) / 4 * 4;
@@ -225,6 +258,8 @@ int run_refine(const Plan* lowp, const float* A32, int64_t lda32, const float* b
             if (last_metric) *last_metric = metric;
             if (!std::isfinite(metric)) return RK_EDIVERGED;
             if (o.tol > 0.0 && metric < o.tol) break;
+            err0[0] = err[0];
+            err0[1] = err[1];
         }
     }
     return RK_OK;
