@@ -223,17 +223,19 @@ def oracle_sample(A_np, b_np, tab, q, alpha_sample, seed, threads):
 
 def sample_alpha(A_np, b_np, tab, q, seed, threads, target_s):
     """Projections per worker so that one oracle round takes about target_s: a first
-    probe warms the call up (pages of A, the thread pool) and is discarded; two warm
-    probes (40 and 200 projections a worker) separate the call's fixed cost (row norms)
-    from the cost of a projection, which is bounded below by a twentieth of the larger
-    probe's average so that a noisy difference cannot ask for an unbounded sample."""
+    probe warms the call up (pages of A, the thread pool) and is discarded; a warm probe
+    grows by fours until it takes at least an eighth of the target, and its own time per
+    projection (the call's fixed cost included, so the sample errs short by at most that
+    share) scales it to the target.  The probes cost at most about two thirds of it."""
     oracle_sample(A_np, b_np, tab, q, 10, seed, threads)
-    _, t1 = oracle_sample(A_np, b_np, tab, q, 40, seed, threads)
-    _, t2 = oracle_sample(A_np, b_np, tab, q, 200, seed, threads)
-    avg = t2 / 200.0
-    per = max((t2 - t1) / 160.0, avg / 20.0, 1e-7)
-    fixed = max(t1 - 40.0 * per, 0.0)
-    return max(10, int(max(target_s - fixed, per) / per))
+    cap = 10 * int(A_np.shape[0])
+    a = 40
+    while True:
+        _, t = oracle_sample(A_np, b_np, tab, q, a, seed, threads)
+        if t >= target_s / 8.0 or a >= cap:
+            break
+        a = min(4 * a, cap)
+    return max(10, min(cap, int(target_s * a / max(t, 1e-9))))
 
 
 def cpu_model():
