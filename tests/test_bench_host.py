@@ -53,3 +53,18 @@ def test_sample_alpha_stays_near_target(monkeypatch, fixed, per, first_extra, ji
 def test_sample_alpha_tiny_target_keeps_a_minimum(monkeypatch):
     monkeypatch.setattr(bench, "oracle_sample", _Fake(0.35, 0.002))
     assert bench.sample_alpha(_A(), None, None, 132, 0, 8, 0.01) == 10
+
+
+def test_algorithmic_bytes_of_the_roofline():
+    """The roofline's numerator: per projection the row, b_i, 1/||A_i||^2 and the alias
+    entry; per round the averaging traffic of the partial iterates written (q of them, or
+    one per CTA for RKA spread over the CTAs)."""
+    n = 10000
+    per_proj = n * 4 + 4 + 4 + 12
+    # the benchmark configuration: 132 workers, alpha = n, 28 rounds (1.4796e12 B)
+    assert bench.algorithmic_bytes(n, 132, n, 28) == 28 * (132 * n * per_proj + 3 * 132 * n * 4)
+    assert bench.algorithmic_bytes(n, 132, n, 28) == 1479582720000
+    # RKA with 4864 workers on 152 SMs: 152 partial iterates a round
+    assert bench.algorithmic_bytes(n, 4864, 1, 85, 4, 152) == 85 * (4864 * per_proj + 3 * 152 * n * 4)
+    # BF16 rows: 2 bytes an element
+    assert bench.algorithmic_bytes(n, 132, 1, 1, 2) == 132 * (n * 2 + 20) + 3 * 132 * n * 4
