@@ -16,6 +16,12 @@ per step); ms_per_step = time to tolerance including the setup.
 bounded sample of the same workload (the paper's own implementation is CPU code
 that is not available, so the oracle serves as the reference).
 
+Other workloads (--workload, one JSON line each): lsq (200000 x 20000 row-scaled
+inconsistent system, the normal-equation criterion per round), precision
+(1e6 x 16000, FP32 against BF16 / FP8 rows with refinement), horizon (80000 x 1000
+inconsistent, error and residual curves), adjoint (the backward pass at
+200000 x 20000), setup (rk_setup alone).
+
 Multi-GPU: the path is run as independent replicas (one per rank, no
 collective in the data path); value sums the replicas' projections over the
 slowest rank's time.
