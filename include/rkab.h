@@ -136,7 +136,14 @@ size_t rk_setup_workspace_bytes(int64_t m, int64_t n);
  *              the caller, must outlive the plan and not be reused while the plan lives
  *   out        receives a host-allocated plan (release with rk_plan_destroy)
  * Limits: 1 <= m < 2^31, 1 <= n < 2^26, lda >= n.  Enqueues the build on `stream`;
- * an all-zero or non-finite A is reported by rk_plan_status (RK_ESETUP). */
+ * an all-zero or non-finite A is reported by rk_plan_status (RK_ESETUP), and so is a
+ * row the law can draw (K_i > 0) whose ||A_i||^2 lies outside [2^-126, 2^126): the
+ * float32 projection of Eq. (alg) cannot take it (1/||A_i||^2 overflows, the products
+ * <A_i, x> underflow).  Eq. (alg) is invariant under scaling a row and its b_i by the
+ * same factor, so such a system is solved after scaling A and b by a power of two
+ * (exact in float32), which leaves x unchanged.  Rows outside that range that the law
+ * never draws (their weight truncates to K_i = 0) keep the plan usable, except for the
+ * cyclic selection, which visits every row (the solve then fails with RK_EINVAL). */
 int rk_setup(const void *A, rk_dtype dt, const float *row_scale, int64_t m, int64_t n,
              int64_t lda, void *workspace, size_t ws_bytes, void *stream, rk_plan **out);
 
@@ -144,8 +151,14 @@ int rk_setup(const void *A, rk_dtype dt, const float *row_scale, int64_t m, int6
  * RK_ESETUP); on success *T_out and *L_out (either may be NULL) receive T and L. */
 int rk_plan_status(const rk_plan *plan, void *stream, uint64_t *T_out, int32_t *L_out);
 
+/* Synchronise `stream` and return ||A||_F^2 of the plan's law: T 2^L, the sum of the integer
+ * row weights (each ||A_i||^2 truncated to the law's bits: about 1e-8 relative below the
+ * exact value for a Gaussian matrix).  Errors as rk_plan_status. */
+int rk_plan_frobenius2(const rk_plan *plan, void *stream, double *fro2);
+
 /* Device addresses of the plan's tables (any may be NULL): K (uint64, m), P (uint64, m),
- * thr64 (uint64, m), alias (uint32, m), inv (float32, m: 1/||A_i||^2, 0 for zero rows). */
+ * thr64 (uint64, m), alias (uint32, m), inv (float32, m: 1/||A_i||^2; 0 for zero rows and
+ * for rows with ||A_i||^2 outside [2^-126, 2^126)). */
 int rk_plan_tables(const rk_plan *plan, const uint64_t **K, const uint64_t **P,
                    const uint64_t **thr64, const uint32_t **alias, const float **inv);
 
@@ -229,13 +242,16 @@ typedef struct {
  *   plan, b, x0, x, q, alpha, rounds, seed, opts   as for rkab_solve
  *   result   where the outcome is written when the solve ends (stream-ordered): any
  *            address cudaMemcpyAsync accepts (device or pinned host); NULL to skip
- * Returns RK_ETOOLARGE when rk_solve_workspace_bytes(plan, q) exceeds the array
- * (q <= 207 at n = 10000 on 152 SMs; any q for RKA), before any device
- * work.  Every GPU that loads the library holds the array until the process exits.
- * The first call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  All calls on a device
- * share the array and it keeps the last call's contents (each call clears the
- * run-state header): calls whose work overlaps on the GPU race on it. */
+ * Options are checked as for rkab_solve (RK_EINVAL).  Returns RK_ETOOLARGE, before any
+ * device work, when the scratch of this launch exceeds the array: about
+ * (r + 1) * ceil(n / 4) * 16 + 256 r bytes with r = q, or r = the SM count for RKA
+ * (alpha = 1) with more workers than SMs (at n = 10000 on 152 SMs: q <= 207 for
+ * alpha > 1, any q for alpha = 1).  Every GPU that loads the library holds the array
+ * until the process exits.  The first call on a device looks up the array's device
+ * address with that device current and keeps it for the life of the process; make
+ * that first call before any stream capture, and make no call after cudaDeviceReset.
+ * All calls on a device share the array and it keeps the last call's contents (each
+ * call clears the run-state header): calls whose work overlaps on the GPU race on it. */
 int rkab_solve_noalloc(const rk_plan *plan, const float *b, const float *x0, float *x, int q,
                        int64_t alpha, int64_t rounds, uint64_t seed, const rk_opts *opts,
                        rk_solve_result *result, void *stream);
@@ -419,6 +435,23 @@ int rk_spectrum(const float *A, int64_t m, int64_t n, int64_t lda, int k, uint64
 int rk_spectrum_ex(const float *A, int64_t m, int64_t n, int64_t lda, int k, uint64_t seed,
                    double fro2, void *workspace, size_t ws_bytes, void *stream, double *out,
                    int *steps_done);
+
+/* s_min = sigma_min^2 / ||A||_F^2 and s_max = sigma_max^2 / ||A||_F^2 of Eq. (best_alpha)
+ * from the 3 doubles rk_spectrum writes (clamped to [0, 1]); either output may be NULL.
+ * RK_EINVAL when ||A||_F^2 (spectrum[2]) is not positive and finite. */
+int rk_spectrum_ratios(const double *spectrum, double *s_min, double *s_max);
+
+/* alpha* of Eq. (best_alpha) for RKA with q workers on A: rk_spectrum_ex (k Lanczos steps,
+ * fro2 as there; rk_plan_frobenius2 gives it from a plan of A), rk_spectrum_ratios and
+ * rk_alpha_star in one call.
+ *   alpha      host <- alpha*
+ *   out        host, 5 doubles or NULL <- [sigma_min^2, sigma_max^2, ||A||_F^2, s_min, s_max]
+ *   steps_done host or NULL <- Lanczos steps taken
+ *   workspace  device, >= rk_spectrum_workspace_bytes(m, n, k), 256-byte aligned
+ * Synchronous, like rk_spectrum.  RK_EINVAL for q < 1 or a zero matrix. */
+int rk_optimal_weight(const float *A, int64_t m, int64_t n, int64_t lda, int q, int k,
+                      uint64_t seed, double fro2, void *workspace, size_t ws_bytes, void *stream,
+                      double *alpha, double *out, int *steps_done);
 
 /* Bytes of device workspace rk_partial_alpha_star needs. */
 size_t rk_partial_alpha_workspace_bytes(int64_t m, int64_t n, int q, int k);

@@ -58,6 +58,7 @@ _SIG = {
                                       ctypes.POINTER(_V), ctypes.POINTER(_V),
                                       ctypes.POINTER(_V)]),
     "rk_plan_destroy": (None, [_V]),
+    "rk_plan_frobenius2": (ctypes.c_int, [_V, _V, ctypes.POINTER(ctypes.c_double)]),
     "rk_sample_indices": (ctypes.c_int, [_V, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                          ctypes.c_uint64, ctypes.c_int64, _V, _V]),
     "rk_sample_indices_ex": (ctypes.c_int, [_V, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
@@ -110,6 +111,12 @@ _SIG = {
     "rk_spectrum_ex": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                       ctypes.c_uint64, ctypes.c_double, _V, ctypes.c_size_t, _V,
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "rk_spectrum_ratios": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "rk_optimal_weight": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_uint64, ctypes.c_double, _V, ctypes.c_size_t,
+                                         _V, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int)]),
     "rk_partial_alpha_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                                            ctypes.c_int]),
     "rk_partial_alpha_star": (ctypes.c_int, [_V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,

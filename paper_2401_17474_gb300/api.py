@@ -7,7 +7,6 @@ Workspaces are allocated here with torch (the library never allocates).
 from __future__ import annotations
 
 import ctypes
-import math
 from dataclasses import dataclass
 
 import torch
@@ -90,10 +89,13 @@ class Plan:
         return int(T.value), int(Lx.value)
 
     def frobenius2(self, stream=None) -> float:
-        """||A||_F^2 of the stored rows from the exact-integer law: T 2^L (each row weight
-        truncated to the law's bits; about 1e-8 relative).  Synchronises."""
-        T, L = self.status(stream)
-        return math.ldexp(float(T), L)
+        """||A||_F^2 of the stored rows from the exact-integer law (rk_plan_frobenius2:
+        T 2^L, each row weight truncated to the law's bits; about 1e-8 relative).
+        Synchronises."""
+        out = ctypes.c_double()
+        check(_lib.load().rk_plan_frobenius2(self._h, _stream(stream), ctypes.byref(out)),
+              "rk_plan_frobenius2")
+        return float(out.value)
 
     def tables(self):
         """Device tensors K (int64 view of uint64), P, thr64, alias (int32 view), inv."""
@@ -380,14 +382,16 @@ class Spectrum:
     lambda_max: float    # estimate of sigma_max(A)^2 (from below)
     fro2: float          # ||A||_F^2
     steps: int           # Lanczos steps taken
+    s_min: float = 0.0   # sigma_min^2 / ||A||_F^2 of Eq. (best_alpha) (rk_spectrum_ratios)
+    s_max: float = 0.0   # sigma_max^2 / ||A||_F^2
 
-    @property
-    def s_min(self) -> float:
-        return self.lambda_min / self.fro2
 
-    @property
-    def s_max(self) -> float:
-        return self.lambda_max / self.fro2
+def _spectrum(out3, steps) -> Spectrum:
+    """Spectrum of rk_spectrum's three doubles, the ratios of Eq. (best_alpha) from C."""
+    arr = (ctypes.c_double * 3)(out3[0], out3[1], out3[2])
+    lo, hi = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(_lib.load().rk_spectrum_ratios(arr, ctypes.byref(lo), ctypes.byref(hi)), "rk_spectrum_ratios")
+    return Spectrum(out3[0], out3[1], out3[2], steps, lo.value, hi.value)
 
 
 def spectrum(A: torch.Tensor, k: int = 32, seed: int = 0, stream=None, fro2=None) -> Spectrum:
@@ -409,14 +413,29 @@ def spectrum(A: torch.Tensor, k: int = 32, seed: int = 0, stream=None, fro2=None
     else:
         check(lib.rk_spectrum_ex(_ptr(A), m, n, A.stride(0), int(k), int(seed), float(fro2), _ptr(ws),
                                  ws.numel(), _stream(stream), out, ctypes.byref(steps)), "rk_spectrum_ex")
-    return Spectrum(out[0], out[1], out[2], steps.value)
+    return _spectrum(out, steps.value)
 
 
 def optimal_weight(A: torch.Tensor, q: int, k: int = 32, seed: int = 0, stream=None, plan=None):
-    """(alpha*, Spectrum): the weight of Eq. (best_alpha) for RKA with q workers on A; with
-    the plan of A, ||A||_F^2 comes from its sampling law instead of a pass over A."""
-    sp = spectrum(A, k, seed, stream, None if plan is None else plan.frobenius2())
-    return alpha_star(q, sp.s_min, sp.s_max), sp
+    """(alpha*, Spectrum): the weight of Eq. (best_alpha) for RKA with q workers on A
+    (rk_optimal_weight); with the plan of A, ||A||_F^2 comes from its sampling law
+    (rk_plan_frobenius2) instead of a pass over A."""
+    if A.dtype != torch.float32 or A.stride(1) != 1 or not A.is_cuda:
+        raise ValueError("A must be a float32 CUDA matrix with unit column stride")
+    m, n = A.shape
+    lib = _lib.load()
+    nbytes = lib.rk_spectrum_workspace_bytes(m, n, int(k))
+    if nbytes == 0:
+        raise RkError(_lib.RK_EINVAL, "rk_spectrum_workspace_bytes")
+    ws = _workspace(nbytes, A.device)
+    fro2 = 0.0 if plan is None else plan.frobenius2(stream)
+    a = ctypes.c_double(0.0)
+    out = (ctypes.c_double * 5)()
+    steps = ctypes.c_int(0)
+    check(lib.rk_optimal_weight(_ptr(A), m, n, A.stride(0), int(q), int(k), int(seed), float(fro2),
+                                _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(a), out,
+                                ctypes.byref(steps)), "rk_optimal_weight")
+    return a.value, Spectrum(out[0], out[1], out[2], steps.value, out[3], out[4])
 
 
 def partial_alpha_star(A: torch.Tensor, q: int, k: int = 8, seed: int = 0, stream=None):
@@ -437,7 +456,7 @@ def partial_alpha_star(A: torch.Tensor, q: int, k: int = 8, seed: int = 0, strea
     check(lib.rk_partial_alpha_star(_ptr(A), m, n, A.stride(0), int(q), int(k), int(seed), _ptr(ws),
                                     ws.numel(), _stream(stream), w, sp), "rk_partial_alpha_star")
     weights = torch.tensor(list(w), dtype=torch.float32, device=A.device)
-    return weights, [Spectrum(sp[3 * g], sp[3 * g + 1], sp[3 * g + 2], 0) for g in range(int(q))]
+    return weights, [_spectrum(sp[3 * g: 3 * g + 3], 0) for g in range(int(q))]
 
 
 def launch_count() -> int:

@@ -67,6 +67,23 @@ SetupWs setup_ws_carve(void* base, int64_t m) {
     return w;
 }
 
+// Row selection: a known mode; per-worker modes need the workers' own streams.
+bool sampling_ok(const rk_opts& o) {
+    if (o.sampling == RK_SAMPLE_FULL) return true;
+    return (o.sampling == RK_SAMPLE_BLOCKS || o.sampling == RK_SAMPLE_CYCLIC) && !o.same_stream;
+}
+
+// Options every solve entry point accepts (rkab_solve, rkab_solve_noalloc, and the
+// solves inside rkab_solve_residual and rkab_adjoint).
+bool solve_opts_valid(const rk_opts& o, int q) {
+    return omega_ok(o.omega, q) && sampling_ok(o) && o.check_every >= 0 && o.round0 >= 0 &&
+           o.timeout_s > 0.0 && !(o.criterion == 1 && !o.x_ref) && o.criterion >= 0 &&
+           o.criterion <= 1 &&
+           (o.lookahead == 0 || o.lookahead == 1 || o.lookahead == 2 || o.lookahead == 4 ||
+            o.lookahead == 6) &&
+           o.cluster_size >= 0 && o.cluster_size <= 16 && (o.cluster_size & (o.cluster_size - 1)) == 0;
+}
+
 }  // namespace rk
 
 using namespace rk;
@@ -91,12 +108,6 @@ void rk_opts_default(rk_opts* o) {
     o->worker_weight = nullptr;
 }
 
-// Row selection: a known mode; per-worker modes need the workers' own streams.
-static bool sampling_ok(const rk_opts& o) {
-    if (o.sampling == RK_SAMPLE_FULL) return true;
-    return (o.sampling == RK_SAMPLE_BLOCKS || o.sampling == RK_SAMPLE_CYCLIC) && !o.same_stream;
-}
-
 const char* rk_strerror(int code) {
     switch (code) {
         case RK_OK: return "ok";
@@ -107,7 +118,8 @@ const char* rk_strerror(int code) {
         case RK_EDIVERGED: return "iterate became non-finite";
         case RK_ECUDA: return "CUDA runtime error";
         case RK_EWORKSPACE: return "workspace too small";
-        case RK_ESETUP: return "plan setup failed on the device (non-finite or all-zero matrix)";
+        case RK_ESETUP: return "plan setup failed on the device (non-finite or all-zero matrix, or a "
+                               "row with ||A_i||^2 outside the float32 range)";
         case RK_ETOOLARGE: return "q x n exceeds the fixed scratch of the allocation-free solve";
         default: return "unknown error";
     }
@@ -209,13 +221,7 @@ int rkab_solve(const rk_plan* plan, const float* b, const float* x0, float* x, i
     rk_opts o;
     rk_opts_default(&o);
     if (opts) o = *opts;
-    if (!omega_ok(o.omega, q) || o.check_every < 0 || o.round0 < 0 ||
-        !(o.timeout_s > 0.0) || (o.criterion == 1 && !o.x_ref) || o.criterion < 0 ||
-        o.criterion > 1 || !(o.lookahead == 0 || o.lookahead == 1 || o.lookahead == 2 ||
-                             o.lookahead == 4 || o.lookahead == 6) ||
-        o.cluster_size < 0 || o.cluster_size > 16 || (o.cluster_size & (o.cluster_size - 1)) != 0 ||
-        !sampling_ok(o))
-        return RK_EINVAL;
+    if (!solve_opts_valid(o, q)) return RK_EINVAL;
     if (((uintptr_t)workspace & 255u) != 0) return RK_EALIGN;
     if (ws_bytes < solve_ws_bytes(&plan->p, q)) return RK_EWORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -312,15 +318,6 @@ int rk_rank2(const float* r, const float* g, const float* y, const float* x, int
     return launch_rank2(r, g, y, x, m, n, G, ldg, static_cast<cudaStream_t>(stream));
 }
 
-static bool valid_opts(const rk_opts& o, int q) {
-    return omega_ok(o.omega, q) && sampling_ok(o) && o.check_every >= 0 && o.round0 >= 0 &&
-           o.timeout_s > 0.0 && !(o.criterion == 1 && !o.x_ref) && o.criterion >= 0 &&
-           o.criterion <= 1 &&
-           (o.lookahead == 0 || o.lookahead == 1 || o.lookahead == 2 || o.lookahead == 4 ||
-            o.lookahead == 6) &&
-           o.cluster_size >= 0 && o.cluster_size <= 16 && (o.cluster_size & (o.cluster_size - 1)) == 0;
-}
-
 size_t rk_adjoint_workspace_bytes(const rk_plan* plan_A, const rk_plan* plan_At, int q_t, int q) {
     if (!plan_A || !plan_At || q < 1 || q_t < 1) return 0;
     return adjoint_ws_bytes(&plan_A->p, &plan_At->p, q_t, q);
@@ -347,7 +344,7 @@ int rkab_adjoint(const rk_plan* plan_A, const rk_plan* plan_At, const float* b, 
     if (opts) oa = *opts;
     ot.criterion = 0;
     oa.criterion = 0;
-    if (!valid_opts(ot, q_t) || !valid_opts(oa, q)) return RK_EINVAL;
+    if (!solve_opts_valid(ot, q_t) || !solve_opts_valid(oa, q)) return RK_EINVAL;
     if (ws_bytes < adjoint_ws_bytes(&pa, &pt, q_t, q)) return RK_EWORKSPACE;
     return run_adjoint(&pa, &pt, b, x, gx, q_t, q, alpha_t, rounds_t, alpha, rounds, seed, ot, oa,
                        grad_b, grad_A, ldg, g, workspace, static_cast<cudaStream_t>(stream));
@@ -383,7 +380,7 @@ int rkab_solve_residual(const rk_plan* plan, const float* A32, int64_t lda32, co
     o.criterion = 0;
     o.check_every = 0;
     o.x_ref = nullptr;
-    if (!valid_opts(o, q)) return RK_EINVAL;
+    if (!solve_opts_valid(o, q)) return RK_EINVAL;
     if (ws_bytes < rk_solve_residual_workspace_bytes(plan, q)) return RK_EWORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint8_t* p = static_cast<uint8_t*>(workspace);
@@ -465,6 +462,26 @@ double rk_alpha_star(int q, double s_min, double s_max) {
     return 2.0 * q / (1.0 + (q - 1) * (s_min + s_max));
 }
 
+int rk_plan_frobenius2(const rk_plan* plan, void* stream, double* fro2) {
+    if (!plan || !fro2) return RK_EINVAL;
+    uint64_t T = 0;
+    int32_t L = 0;
+    const int rc = rk_plan_status(plan, stream, &T, &L);
+    if (rc != RK_OK) return rc;
+    *fro2 = std::ldexp((double)T, L);   // sum of the integer row weights K_i 2^L
+    return RK_OK;
+}
+
+int rk_spectrum_ratios(const double* spectrum, double* s_min, double* s_max) {
+    if (!spectrum || !(spectrum[2] > 0.0) || !std::isfinite(spectrum[2])) return RK_EINVAL;
+    // s = sigma^2 / ||A||_F^2 (Eq. (best_alpha)), clamped to [0, 1] against rounding
+    const double lo = std::fmin(std::fmax(spectrum[0] / spectrum[2], 0.0), 1.0);
+    const double hi = std::fmin(std::fmax(spectrum[1] / spectrum[2], 0.0), 1.0);
+    if (s_min) *s_min = lo;
+    if (s_max) *s_max = hi;
+    return RK_OK;
+}
+
 static int lanczos_steps(int64_t m, int64_t n, int k) {   // at most min(m, n) are of use
     const int64_t r = m < n ? m : n;
     return (int)(k < r ? k : r);
@@ -496,6 +513,28 @@ int rk_spectrum_ex(const float* A, int64_t m, int64_t n, int64_t lda, int k, uin
                         steps_done, fro2);
 }
 
+int rk_optimal_weight(const float* A, int64_t m, int64_t n, int64_t lda, int q, int k, uint64_t seed,
+                      double fro2, void* workspace, size_t ws_bytes, void* stream, double* alpha,
+                      double* out, int* steps_done) {
+    if (!alpha || q < 1) return RK_EINVAL;
+    double sp[3];
+    const int rc = rk_spectrum_ex(A, m, n, lda, k, seed, fro2, workspace, ws_bytes, stream, sp, steps_done);
+    if (rc != RK_OK) return rc;
+    double s_min = 0.0, s_max = 0.0;
+    if (rk_spectrum_ratios(sp, &s_min, &s_max) != RK_OK) return RK_EINVAL;   // a zero matrix
+    const double a = rk_alpha_star(q, s_min, s_max);
+    if (!(a > 0.0)) return RK_EINVAL;
+    *alpha = a;
+    if (out) {
+        out[0] = sp[0];
+        out[1] = sp[1];
+        out[2] = sp[2];
+        out[3] = s_min;
+        out[4] = s_max;
+    }
+    return RK_OK;
+}
+
 size_t rk_partial_alpha_workspace_bytes(int64_t m, int64_t n, int q, int k) {
     if (m < 1 || n < 1 || q < 1 || q > m || k < 1 || k > 512) return 0;
     const int64_t rows = (m + q - 1) / q + 1;   // the largest block
@@ -516,9 +555,8 @@ int rk_partial_alpha_star(const float* A, int64_t m, int64_t n, int64_t lda, int
         const int rc = run_spectrum(A + lo * lda, hi - lo, n, lda, lanczos_steps(hi - lo, n, k), seed,
                                     workspace, static_cast<cudaStream_t>(stream), out, nullptr);
         if (rc != RK_OK) return rc;
-        if (!(out[2] > 0.0)) return RK_EINVAL;   // a zero block has no law
-        const double s_min = std::fmin(std::fmax(out[0] / out[2], 0.0), 1.0);
-        const double s_max = std::fmin(std::fmax(out[1] / out[2], 0.0), 1.0);
+        double s_min = 0.0, s_max = 0.0;
+        if (rk_spectrum_ratios(out, &s_min, &s_max) != RK_OK) return RK_EINVAL;   // a zero block has no law
         weights[g] = (float)rk_alpha_star(q, s_min, s_max);
         if (spectra) {
             spectra[3 * g] = out[0];

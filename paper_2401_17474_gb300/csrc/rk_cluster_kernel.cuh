@@ -141,8 +141,10 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
     __syncthreads();
     // every CTA of the cluster has its barriers ready before anyone sends to it
     cluster_sync_all();
-    const bool setup_ok = p.setup->status == 0;
-    if (!setup_ok && tid == 0) set_status(status, RK_ESETUP);
+    // a failed plan, or a cyclic sweep over rows the float32 projection cannot take
+    const bool cyc_bad = p.sampling == RK_SAMPLE_CYCLIC && p.setup->range_rows != 0;
+    const bool setup_ok = p.setup->status == 0 && !cyc_bad;
+    if (!setup_ok && tid == 0) set_status(status, cyc_bad ? RK_EINVAL : RK_ESETUP);
 
     // this CTA's chunk of every row: slices [c0, c0 + nl)
     const int c0 = (int)crank * cp.chunk;

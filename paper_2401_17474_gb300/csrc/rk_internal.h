@@ -22,6 +22,9 @@ struct SetupInfo {
     int pad0;
     uint64_t T;      // sum_i K_i
     uint32_t nl, nh; // number of light / heavy buckets
+    uint32_t range_rows;  // nonzero rows with ||A_i||^2 outside [2^-126, 2^126): no float32
+                          // reciprocal (inv_i = 0); never drawn when the plan succeeds
+    uint32_t pad1;
 };
 
 // Pointers into the setup workspace.  The first group is the plan's tables
@@ -89,7 +92,11 @@ int launch_sample_indices_ex(const Plan* plan, uint64_t seed, uint32_t worker, u
                              uint32_t stream_id, int sampling, uint64_t t0, int64_t count,
                              uint32_t* out, cudaStream_t st);
 int v_rows(int q);
-size_t solve_ws_bytes(const Plan* plan, int q);
+int v_rows_for(int q, int64_t alpha);
+size_t solve_ws_bytes(const Plan* plan, int q);                        // any alpha
+size_t solve_ws_bytes_for(const Plan* plan, int q, int64_t alpha);     // what (q, alpha) uses
+bool sampling_ok(const rk_opts& o);
+bool solve_opts_valid(const rk_opts& o, int q);                        // the solves' option checks
 int launch_solve(const SolveArgs& a, cudaStream_t st);
 int launch_sample_indices(const Plan* plan, uint64_t seed, uint32_t worker, uint32_t stream_id,
                           uint64_t t0, int64_t count, uint32_t* out, cudaStream_t st);

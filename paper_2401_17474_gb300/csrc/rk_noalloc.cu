@@ -17,7 +17,10 @@
 // call made on that device; that first call should therefore come before any
 // stream capture.  All calls on a device share the array and it keeps the last
 // call's contents: the run-state header is cleared by every call, and calls
-// whose work overlaps on the GPU race on the array.
+// whose work overlaps on the GPU race on the array.  The looked-up address is
+// cached for the life of the process: it does not survive cudaDeviceReset (or
+// any other teardown of the device's primary context), after which this entry
+// point must not be called.
 #include <cstddef>
 #include <cstdint>
 #include <mutex>
@@ -57,16 +60,13 @@ extern "C" int rkab_solve_noalloc(const rk_plan* plan, const float* b, const flo
                                   int q, int64_t alpha, int64_t rounds, uint64_t seed,
                                   const rk_opts* opts, rk_solve_result* result, void* stream) {
     if (!plan || !b || !x0 || !x || q < 1 || alpha < 1 || rounds < 0) return RK_EINVAL;
-    // the same layout as the rkab_solve workspace, which must fit the fixed array
-    if (solve_ws_bytes(&plan->p, q) > (size_t)RK_NOALLOC_SCRATCH_BYTES) return RK_ETOOLARGE;
     rk_opts o;
     rk_opts_default(&o);
     if (opts) o = *opts;
-    if (!omega_ok(o.omega, q) || o.check_every < 0 || o.round0 < 0 ||
-        !(o.timeout_s > 0.0) || (o.criterion == 1 && !o.x_ref) || o.criterion < 0 ||
-        o.criterion > 1 || o.sampling < RK_SAMPLE_FULL || o.sampling > RK_SAMPLE_CYCLIC ||
-        (o.sampling != RK_SAMPLE_FULL && o.same_stream))
-        return RK_EINVAL;
+    if (!solve_opts_valid(o, q)) return RK_EINVAL;   // the checks of rkab_solve
+    // the layout of the rkab_solve workspace, with the rows of V this launch uses (one
+    // per SM for RKA with more workers than SMs), must fit the fixed array
+    if (solve_ws_bytes_for(&plan->p, q, alpha) > (size_t)RK_NOALLOC_SCRATCH_BYTES) return RK_ETOOLARGE;
     void* scratch = nullptr;
     const int rc0 = scratch_address(&scratch);
     if (rc0 != RK_OK) return rc0;

@@ -392,7 +392,8 @@ __global__ void __launch_bounds__(NT) row_weight_staged_kernel(const uint8_t* __
 }
 
 // K_i = R_i >> (L + 102 - 2 e_i); L = H + ceil(log2 m) - 62; and
-// inv_i = 1 / ||A_i||^2 in float32 (0 for a zero row).
+// inv_i = 1 / ||A_i||^2 in float32; 0 for a zero row and for a row whose ||A_i||^2 lies
+// outside [2^-126, 2^126) (counted in range_rows; the plan fails if the law can draw it).
 __global__ void weights_to_k_kernel(int64_t m, SetupWs ws) {
     const int H = ws.info->H;
     if (H == kNoRows) {  // all rows zero: no law
@@ -419,7 +420,16 @@ __global__ void weights_to_k_kernel(int64_t m, SetupWs ws) {
             K = (sh >= 128) ? 0 : (uint64_t)(R >> sh);  // sh >= 0 by construction of L
             // 1 / ||A_i||^2 with ||A_i||^2 = R 2^(2e - 102) (R rounded to double once)
             const double rd = (double)(uint64_t)(R >> 64) * 18446744073709551616.0 + (double)(uint64_t)R;
-            inv = (float)(1.0 / ldexp(rd, 2 * e - 102));
+            const double w = ldexp(rd, 2 * e - 102);
+            if (w >= 0x1p-126 && w < 0x1p126) {
+                inv = (float)(1.0 / w);
+            } else {
+                // outside the float32 range of the projection: 1/||A_i||^2 would overflow
+                // (or underflow), and the row's products with x underflow; the solve
+                // cannot project on such a row, so a plan that can draw one fails
+                atomicAdd(&ws.info->range_rows, 1u);
+                if (K != 0) atomicCAS(&ws.info->status, 0, RK_EINVAL);
+            }
         }
         ws.K[i] = K;
         ws.inv[i] = inv;

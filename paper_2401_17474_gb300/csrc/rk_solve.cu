@@ -162,7 +162,7 @@ static KParams base_params(const SolveArgs& a) {
     p.x = a.x;
     p.V = a.V;
     p.ldv = a.ldv;
-    const int rows = v_rows(a.q);
+    const int rows = v_rows_for(a.q, a.alpha);
     p.xbuf = a.V + (size_t)rows * (size_t)a.ldv;
     p.chkpart = a.V + (size_t)(rows + 1) * (size_t)a.ldv;
     p.vrows = a.q;
@@ -332,25 +332,42 @@ int launch_sample_indices(const Plan* plan, uint64_t seed, uint32_t worker, uint
     return cudaGetLastError() == cudaSuccess ? RK_OK : RK_ECUDA;
 }
 
-// Rows of V a solve with q workers needs: one per CTA that holds displacements --
-// q for one or two workers per SM and for cluster workers (q is then at most twice
-// the SM count), the SM count when RKA spreads more workers over the CTAs.
-int v_rows(int q) {
+static int device_sms() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 256;
+    return sms > 0 ? sms : 256;
+}
+
+// Rows of V a solve with q workers may need whatever alpha is: one per CTA that holds
+// displacements -- q for one or two workers per SM and for cluster workers (q is then
+// at most twice the SM count), the SM count when RKA spreads more workers over the CTAs.
+int v_rows(int q) {
+    const int sms = device_sms();
     return q < 2 * sms ? q : 2 * sms;
 }
 
-size_t solve_ws_bytes(const Plan* plan, int q) {
+// Rows of V the launch for (q, alpha) uses: the SM count for RKA with more workers than
+// SMs (one CTA per SM sums its share of the workers), else q.
+int v_rows_for(int q, int64_t alpha) {
+    const int sms = device_sms();
+    if (alpha == 1 && q > sms) return sms;
+    return q < 2 * sms ? q : 2 * sms;
+}
+
+static size_t ws_bytes_rows(const Plan* plan, int rows) {
     const int64_t n4 = (plan->n + 3) / 4;
     const int64_t ldv = n4 * 4;
-    const int rows = v_rows(q);
     // status | V (rows x ldv) and the average (ldv) | per-CTA check partials (a float4
     // for each of up to kClusterMax CTAs per row of V)
     return align256(sizeof(SolveInfo)) + align256((size_t)(rows + 1) * (size_t)ldv * sizeof(float) +
                                                   (size_t)rows * kClusterMax * 4 * sizeof(float));
+}
+
+size_t solve_ws_bytes(const Plan* plan, int q) { return ws_bytes_rows(plan, v_rows(q)); }
+
+size_t solve_ws_bytes_for(const Plan* plan, int q, int64_t alpha) {
+    return ws_bytes_rows(plan, v_rows_for(q, alpha));
 }
 
 }  // namespace rk

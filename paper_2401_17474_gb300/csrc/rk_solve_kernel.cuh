@@ -569,6 +569,12 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
         if (tid == 0) set_status(status, RK_ESETUP);
         return;
     }
+    // the cyclic sweep visits every row, also those whose ||A_i||^2 lies outside the
+    // float32 range of the projection (never drawn by the random selections)
+    if (p.sampling == RK_SAMPLE_CYCLIC && p.setup->range_rows != 0) {
+        if (tid == 0) set_status(status, RK_EINVAL);
+        return;
+    }
     if (warp == NW) {
         producer_loop<ELT, JAC>(p, stages, full, empty, meta, ctrl, pbuf);
         return;
