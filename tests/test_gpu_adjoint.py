@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 import rk_inputs
+from _parity import assert_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -63,7 +64,7 @@ def test_min_norm_solve_matches_oracle(rk, inc):
     At = np.ascontiguousarray(s.A.T)
     yo = oracle.rkab(At, -xt.astype(np.float64), np.zeros(3000), q=4, alpha=50, rounds=6, seed=7,
                      tab=oracle.table(At), stream=1)
-    assert _rel(gb.cpu().numpy(), yo) < TOL
+    assert_close(gb.cpu().numpy(), yo, TOL)
 
 
 def test_adjoint_at_forward_point_matches_qr(rk, inc):
@@ -74,9 +75,9 @@ def test_adjoint_at_forward_point_matches_qr(rk, inc):
     gx = x - _dev(xt)
     gA, gb, g = rk.Adjoint(plan, cfg).backward(_dev(s.b), x, gx)
     rA, rb, rg = oracle.lstsq_adjoint(s.A, s.b, x.cpu().numpy(), xt)
-    assert _rel(gb.cpu().numpy(), rb) < TOL
-    assert _rel(g.cpu().numpy(), rg) < TOL
-    assert _rel(gA.cpu().numpy(), rA) < TOL
+    assert_close(gb.cpu().numpy(), rb, TOL)
+    assert_close(g.cpu().numpy(), rg, TOL)
+    assert_close(gA.cpu().numpy(), rA, TOL)
 
 
 def test_autograd_matches_finite_differences(rk):

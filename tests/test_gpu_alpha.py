@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 import rk_inputs
+from _parity import assert_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -74,8 +75,7 @@ def test_rka_optimal_weight_matches_oracle(rk, q, rounds):
     assert info.status == 0
     x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=q, alpha=1, rounds=rounds,
                       seed=5, tab=tab, omega=float(np.float32(a)))
-    err = np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o)
-    assert err < 1e-4
+    assert_close(x.cpu().numpy(), x_o, 1e-4)
 
 
 def test_rka_optimal_weight_reaches_tolerance_faster(rk):
@@ -167,8 +167,7 @@ def test_worker_weights_match_oracle(rk, q, alpha, rounds, sampling, cluster):
     x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=q, alpha=alpha,
                       rounds=rounds, seed=3, tab=tab, sampling=sampling,
                       worker_weight=u.astype(np.float64))
-    err = np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o)
-    assert err < 1e-4
+    assert_close(x.cpu().numpy(), x_o, 1e-4)
 
 
 @pytest.mark.parametrize("q,sampling", [(4, "full"), (16, "blocks")])
@@ -188,7 +187,7 @@ def test_partial_alpha_rka_matches_oracle(rk, q, sampling):
     assert info.status == 0
     x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(60), q=q, alpha=1, rounds=50,
                       seed=7, tab=tab, sampling=sampling, worker_weight=w_o)
-    assert np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o) < 1e-4
+    assert_close(x.cpu().numpy(), x_o, 1e-4)
     xs = _dev(s.x_star)
     lmin, lmax, fro2 = oracle.spectrum(s.A)
     a = oracle.alpha_star(q, lmin / fro2, lmax / fro2)

@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 import rk_inputs
+from _parity import assert_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,7 +46,7 @@ def test_cluster_workers_match_oracle(rk, C, lookahead, m, n, q, alpha, rounds):
     assert info.status == 0 and info.rounds_done == rounds
     xo = oracle.rkab(s.A, s.b.astype(np.float64), x0.astype(np.float64), q=q, alpha=alpha,
                      rounds=rounds, seed=17, tab=tab)
-    assert _rel(x.cpu().numpy(), xo) < TOL
+    assert_close(x.cpu().numpy(), xo, TOL)
 
 
 @pytest.mark.parametrize("kind", ["bf16", "fp8"])
@@ -60,7 +61,7 @@ def test_cluster_workers_on_stored_rows(rk, kind):
     assert info.status == 0
     xo = oracle.rkab(low, s.b.astype(np.float64), np.zeros(2000), q=3, alpha=40, rounds=3, seed=4,
                      tab=tab)
-    assert _rel(x.cpu().numpy(), xo) < TOL
+    assert_close(x.cpu().numpy(), xo, TOL)
 
 
 def test_cluster_rk_converges_with_stop_rule(rk):
@@ -86,4 +87,31 @@ def test_long_row_cluster_workers_match_oracle(rk, C):
     assert info.status == 0 and info.rounds_done == 3
     xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(n), q=q, alpha=40, rounds=3, seed=5,
                      tab=tab)
-    assert _rel(x.cpu().numpy(), xo) < TOL
+    assert_close(x.cpu().numpy(), xo, TOL)
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16", "fp8"])
+@pytest.mark.parametrize("m,n,alpha,shape", [
+    (300, 50000, 40, "128 threads x 8 slices"),     # 784 slices a CTA (A^T rows of 50000)
+    (120, 200000, 30, "256 threads x 13 slices"),   # 3128 slices a CTA (A^T rows of 200000)
+])
+def test_adjoint_length_rows_match_oracle(rk, kind, m, n, alpha, shape):
+    """The cluster instantiations the adjoint's minimum-norm solve runs on (rows of A^T
+    as long as the 50000 x 5000 and 200000 x 20000 differentiation workloads give: six
+    workers of 16-CTA clusters, as the benchmark launches them), on float32, BF16 and FP8
+    rows: the same draws as the oracle and x within 1e-4, every element."""
+    s = rk_inputs.gaussian_system(m, n, seed=n + 3)
+    A = _dev(s.A)
+    if kind == "f32":
+        plan, low = rk.rk_setup(A), s.A
+    else:
+        Aq, sc = rk.quantize(A, kind)
+        plan = rk.rk_setup(Aq, kind, sc)
+        low = oracle.quantize_bf16(s.A)[1] if kind == "bf16" else oracle.quantize_fp8(s.A)[2]
+    q = 6
+    x, info = rk.rkab_solve(plan, _dev(s.b), q=q, alpha=alpha, rounds=3, seed=11, cluster_size=16,
+                            check_every=0)
+    assert info.status == 0 and info.rounds_done == 3
+    xo = oracle.rkab(low, s.b.astype(np.float64), np.zeros(n), q=q, alpha=alpha, rounds=3, seed=11,
+                     tab=oracle.table(low))
+    assert_close(x.cpu().numpy(), xo, TOL, what=f"{kind} {shape}")

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import rk_inputs
+from _parity import assert_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -52,10 +53,14 @@ def _check_tables(rk, A_np, plan=None):
     assert np.array_equal(thr, tab.thr64)
     assert np.array_equal(al, tab.alias)
     inv = t["inv"].cpu().numpy()
+    assert np.all(np.isfinite(inv))
     w = oracle.row_norms(A_np)
-    nz = w > 0
-    np.testing.assert_allclose(inv[nz], (1.0 / w[nz]).astype(np.float32), rtol=2e-7)
-    assert np.all(inv[~nz] == 0)
+    # rows whose ||A_i||^2 has a float32 reciprocal get it; zero rows and rows outside
+    # [2^-126, 2^126) (never drawn when the plan succeeds) get 0
+    ok = (w >= 2.0 ** -126) & (w < 2.0 ** 126)
+    rel = np.abs(inv[ok].astype(np.float64) * w[ok] - 1.0)
+    assert np.all(rel <= 2.0 ** -24 * 1.01), rel.max()
+    assert np.all(inv[~ok] == 0)
     return plan, tab
 
 
@@ -101,9 +106,70 @@ def test_tables_bit_exact_long_rows(rk, m, n, special):
         A *= (10.0 ** rng.uniform(-2, 2, size=(m, 1))).astype(np.float32)
     elif special == "tiny_values":
         A[::3] = (A[::3] * 1e-41).astype(np.float32)   # subnormal rows
-        A[1::3, :5] *= np.float32(1e30)                   # the rest of the row floors to 0
+        A[1::3, :5] *= np.float32(2.0 ** 59)              # the rest of the row floors to 0
+        # (||A_i||^2 stays below 2^126, the float32 range of the projection)
         A[2::3, :3] *= np.float32(2.0 ** 20)              # entries below 2^-5 floor to nonzero terms
     _check_tables(rk, A)
+
+
+def _tiny_system(m, n, seed):
+    """A system whose every row lies below the float32 range of the projection
+    (entries about 1e-41, subnormal; ||A_i||^2 about 1e-81), b = fl32(A x*)."""
+    rng = np.random.default_rng(seed)
+    A = (rng.standard_normal((m, n)) * 1e-41).astype(np.float32)
+    x_star = rng.standard_normal(n)
+    b = (A.astype(np.float64) @ x_star).astype(np.float32)
+    return A, b
+
+
+def test_rows_below_float32_range_are_refused(rk):
+    """Rows the law draws whose ||A_i||^2 < 2^-126: no float32 reciprocal exists and the
+    products <A_i, x> underflow, so the plan fails (RK_ESETUP) and a solve on it reports
+    RK_ESETUP instead of projecting with an infinite scale."""
+    A, b = _tiny_system(300, 12, seed=5)
+    plan = rk.rk_setup(_padded(A, rk))
+    with pytest.raises(rk.RkError) as e:
+        plan.status()
+    assert e.value.code == -8
+    x, info = rk.rkab_solve(plan, _dev(b), q=2, alpha=10, rounds=2, seed=1, raise_on_error=False)
+    assert info.status == -8
+
+
+def test_subnormal_system_scaled_into_range_matches_oracle(rk):
+    """The same all-subnormal system scaled by 2^120 (exact in float32; Eq. (alg) is
+    invariant under scaling a row and its b_i) solves on the GPU and equals the FP64
+    oracle run on the unscaled system: same law (the integer weights are invariant
+    under power-of-two scaling), same draws, x within 1e-4."""
+    A, b = _tiny_system(300, 12, seed=5)
+    s2 = np.float32(2.0 ** 120)
+    A2, b2 = A * s2, b * s2
+    assert np.array_equal(A2 / s2, A) and np.array_equal(b2 / s2, b)
+    tab = oracle.table(A)
+    plan = rk.rk_setup(_padded(A2, rk))
+    assert plan.status() == (tab.T, tab.L + 240)
+    x, info = rk.rkab_solve(plan, _dev(b2), q=3, alpha=20, rounds=6, seed=4, check_every=0)
+    assert info.status == 0
+    xo = oracle.rkab(A, b.astype(np.float64), np.zeros(12), q=3, alpha=20, rounds=6, seed=4, tab=tab)
+    assert_close(x.cpu().numpy(), xo, TOL)
+
+
+def test_out_of_range_rows_never_drawn(rk):
+    """Rows below the float32 range in a matrix whose law never draws them (K_i = 0):
+    the plan works and the solve matches the oracle; the cyclic sweep, which would visit
+    them, is refused with RK_EINVAL."""
+    s = rk_inputs.gaussian_system(2000, 100, seed=2)
+    A = s.A.copy()
+    A[::50] *= np.float32(1e-41)
+    b = (A.astype(np.float64) @ s.x_star.astype(np.float64)).astype(np.float32)
+    plan, tab = _check_tables(rk, A)
+    assert np.all(tab.K[::50] == 0)
+    x, info = rk.rkab_solve(plan, _dev(b), q=4, alpha=30, rounds=5, seed=6, check_every=0)
+    assert info.status == 0
+    xo = oracle.rkab(A, b.astype(np.float64), np.zeros(100), q=4, alpha=30, rounds=5, seed=6, tab=tab)
+    assert_close(x.cpu().numpy(), xo, TOL)
+    x, info = rk.rkab_solve(plan, _dev(b), q=4, alpha=30, rounds=2, seed=6, sampling="cyclic",
+                            raise_on_error=False)
+    assert info.status == -1
 
 
 @pytest.mark.parametrize("n", [9, 3000])
@@ -157,7 +223,7 @@ def test_c1_rk_and_rka_match_oracle(rk, c1, q, k):
     assert info.status == 0
     xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=q, alpha=1, rounds=k, seed=0,
                      tab=tab)
-    assert _rel(x.cpu().numpy(), xo) < TOL
+    assert_close(x.cpu().numpy(), xo, TOL)
 
 
 @pytest.mark.parametrize("m,n,q,alpha,rounds,omega", [
@@ -180,7 +246,7 @@ def test_rkab_matches_oracle(rk, m, n, q, alpha, rounds, omega):
     assert info.status == 0 and info.rounds_done == rounds
     xo = oracle.rkab(s.A, s.b.astype(np.float64), x0.astype(np.float64), q=q, alpha=alpha,
                      rounds=rounds, seed=77, tab=tab, omega=omega)
-    assert _rel(x.cpu().numpy(), xo) < TOL
+    assert_close(x.cpu().numpy(), xo, TOL)
 
 
 @pytest.mark.parametrize("lookahead", [1, 2, 4])
@@ -198,7 +264,7 @@ def test_lookahead_groups_match_oracle(rk, lookahead, m, n, q, alpha, rounds):
     assert info.status == 0
     xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(n), q=q, alpha=alpha, rounds=rounds,
                      seed=13, tab=tab)
-    assert _rel(x.cpu().numpy(), xo) < TOL
+    assert_close(x.cpu().numpy(), xo, TOL)
 
 
 def test_special_cases_on_gpu(rk, c1):
@@ -206,10 +272,10 @@ def test_special_cases_on_gpu(rk, c1):
     # q = 1 RKAB with alpha = 30 is RK over 30 * rounds projections
     x1, _ = rk.rkab_solve(plan, b, q=1, alpha=30, rounds=5, seed=3)
     xo = oracle.rk(s.A, s.b.astype(np.float64), np.zeros(100), 150, 3, tab)
-    assert _rel(x1.cpu().numpy(), xo) < TOL
+    assert_close(x1.cpu().numpy(), xo, TOL)
     # all workers on one stream average identical iterates: equals RK
     x2, _ = rk.rkab_solve(plan, b, q=6, alpha=30, rounds=5, seed=3, same_stream=True)
-    assert _rel(x2.cpu().numpy(), xo) < TOL
+    assert_close(x2.cpu().numpy(), xo, TOL)
     # rounds = 0 returns x0
     x0 = torch.randn(100, device="cuda")
     x3, _ = rk.rkab_solve(plan, b, x0, q=2, alpha=4, rounds=0, seed=1)
@@ -286,7 +352,7 @@ def test_full_size_sampled_parity(rk):
     x, info = rk.rkab_solve(plan, b, q=q, alpha=10, rounds=1, seed=0)
     xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(n), q=q, alpha=10, rounds=1, seed=0,
                      tab=tab, threads=8)
-    assert _rel(x.cpu().numpy(), xo) < TOL
+    assert_close(x.cpu().numpy(), xo, TOL)
     xs = _dev(s.x_star)
     x, info = rk.rkab_solve(plan, b, q=q, alpha=n, rounds=400, seed=0, x_ref=xs, tol=1e-6)
     assert info.status == 0 and info.last_metric < 1e-6, info
@@ -299,7 +365,7 @@ def test_full_size_sampled_parity(rk):
     x, info = rk.rka_solve(plan, b, q=qa, rounds=2, seed=0, omega=w, check_every=0)
     xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(n), q=qa, alpha=1, rounds=2, seed=0,
                      tab=tab, omega=float(np.float32(w)), threads=8)
-    assert _rel(x.cpu().numpy(), xo) < TOL
+    assert_close(x.cpu().numpy(), xo, TOL)
     x, info = rk.rka_solve(plan, b, q=qa, rounds=400, seed=0, omega=w, x_ref=xs, tol=1e-6)
     assert info.status == 0 and info.last_metric < 1e-6 and info.rounds_done < 120, info
 
@@ -320,7 +386,7 @@ def test_lsq_size_sampled_parity(rk):
     assert info.status == 0
     xo = oracle.rkab(A_np, b_np.astype(np.float64), np.zeros(n), q=q, alpha=3, rounds=1, seed=0,
                      tab=tab, threads=8)
-    assert _rel(x.cpu().numpy(), xo) < TOL
+    assert_close(x.cpu().numpy(), xo, TOL)
     _, norms = rk.rk_residual(A, b, x)
     _, rn, an = oracle.residual(A_np, b_np, x.cpu().numpy().astype(np.float64))
     nn = norms.cpu().numpy()
@@ -358,7 +424,7 @@ def test_more_workers_than_sms_matches_oracle(rk, alpha, rounds):
     assert info.status == 0 and info.rounds_done == rounds
     x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=q, alpha=alpha,
                       rounds=rounds, seed=3, tab=tab)
-    assert _rel(x.cpu().numpy(), x_o) < TOL
+    assert_close(x.cpu().numpy(), x_o, TOL)
     with pytest.raises(rk.RkError) as e:
         rk.rkab_solve(plan, _dev(s.b), q=2 * sms + 1, alpha=2, rounds=1)
     assert e.value.code == -3
@@ -380,7 +446,7 @@ def test_rka_many_workers_matches_oracle(rk, mult, extra, omega):
     assert info.status == 0 and info.rounds_done == 15
     x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(200), q=q, alpha=1, rounds=15,
                       seed=9, tab=tab, omega=omega)
-    assert _rel(x.cpu().numpy(), x_o) < TOL
+    assert_close(x.cpu().numpy(), x_o, TOL)
 
 
 @pytest.mark.parametrize("sampling", ["blocks", "cyclic"])
@@ -409,7 +475,7 @@ def test_selection_solve_matches_oracle(rk, sampling, q, alpha, rounds):
     assert info.status == 0
     x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=q, alpha=alpha, rounds=rounds,
                       seed=7, tab=tab, sampling=sampling)
-    assert _rel(x.cpu().numpy(), x_o) < TOL
+    assert_close(x.cpu().numpy(), x_o, TOL)
 
 
 def test_row_weights_and_many_worker_blocks_match_oracle(rk):
@@ -423,13 +489,15 @@ def test_row_weights_and_many_worker_blocks_match_oracle(rk):
                             row_weight=_dev(w))
     x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=5, alpha=40, rounds=5, seed=2,
                       tab=tab, row_weight=w.astype(np.float64))
-    assert info.status == 0 and _rel(x.cpu().numpy(), x_o) < TOL
+    assert info.status == 0
+    assert_close(x.cpu().numpy(), x_o, TOL)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     q = 2 * sms + 5
     x, info = rk.rka_solve(plan, _dev(s.b), q=q, rounds=10, seed=4, check_every=0, sampling="blocks")
     x_o = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=q, alpha=1, rounds=10, seed=4,
                       tab=tab, sampling="blocks")
-    assert info.status == 0 and _rel(x.cpu().numpy(), x_o) < TOL
+    assert info.status == 0
+    assert_close(x.cpu().numpy(), x_o, TOL)
 
 
 def test_zero_weight_block_is_refused(rk):
@@ -458,7 +526,7 @@ def test_residual_stopping_rules(rk):
                                                seed=2)
     assert 0 < rounds < 400 and rounds % 3 == 0 and 0 <= metric < 1e-6
     x_o = oracle.rkab(s.A, b64, np.zeros(100), q=4, alpha=100, rounds=rounds, seed=2, tab=tab)
-    assert _rel(x.cpu().numpy(), x_o) < TOL
+    assert_close(x.cpu().numpy(), x_o, TOL)
     _, rn, _ = oracle.residual(s.A, b64, x.cpu().numpy().astype(np.float64))
     assert metric == pytest.approx(rn / np.linalg.norm(b64), rel=1e-6)
     # least squares: ||A^T r|| / (||A||_F ||r||) on an inconsistent system, uneven stretches
@@ -470,7 +538,7 @@ def test_residual_stopping_rules(rk):
                                                check_every=7, tol=0.0, criterion="normal", seed=4)
     assert rounds == 30
     x_o = oracle.rkab(si.A, bi, np.zeros(100), q=3, alpha=50, rounds=30, seed=4, tab=tabi)
-    assert _rel(x.cpu().numpy(), x_o) < TOL
+    assert_close(x.cpu().numpy(), x_o, TOL)
     _, rn, an = oracle.residual(si.A, bi, x.cpu().numpy().astype(np.float64))
     fro = np.sqrt(np.sum(si.A.astype(np.float64) ** 2))
     assert metric == pytest.approx(an / (fro * rn), rel=1e-5)
@@ -490,7 +558,7 @@ def test_degenerate_shapes_match_oracle(rk, m, n, q, alpha):
     assert info.status == 0
     x_o = oracle.rkab(A, b.astype(np.float64), np.zeros(n), q=q, alpha=alpha, rounds=5, seed=8,
                       tab=tab)
-    assert _rel(x.cpu().numpy(), x_o) < TOL
+    assert_close(x.cpu().numpy(), x_o, TOL)
 
 
 def test_empty_system_is_refused(rk):
@@ -498,3 +566,23 @@ def test_empty_system_is_refused(rk):
         rk.rk_setup(torch.zeros((0, 4), dtype=torch.float32, device="cuda"))
     with pytest.raises((rk.RkError, ValueError)):
         rk.rk_setup(torch.zeros((4, 0), dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("q,alpha,omega_per_q", [(4, 100, 1.9), (8, 10, 1.9), (200, 1, 1.95)])
+def test_divergence_is_reported(rk, c1, q, alpha, omega_per_q):
+    """A relaxation beyond the stable range (Section 3.4.2: RKAB can diverge for weights
+    above 1) drives the float32 iterate to overflow: the solve stops at the next check
+    with RK_EDIVERGED, a host-visible status (no device fault), and the next solve on the
+    same plan and context runs normally and matches the oracle."""
+    s, plan, tab, b = c1
+    x, info = rk.rkab_solve(plan, b, q=q, alpha=alpha, rounds=400, seed=2,
+                            omega=omega_per_q * q, raise_on_error=False)
+    assert info.status == -5, info
+    assert info.rounds_done < 400
+    # the check's float32 ||x||^2 overflowed: x itself may still be finite
+    assert not torch.isfinite(x).all() or float((x.double() ** 2).sum()) > 3.4e38
+    x, info = rk.rkab_solve(plan, b, q=4, alpha=20, rounds=5, seed=3, check_every=1)
+    assert info.status == 0 and info.rounds_done == 5
+    xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(100), q=4, alpha=20, rounds=5,
+                     seed=3, tab=tab)
+    assert_close(x.cpu().numpy(), xo, TOL)

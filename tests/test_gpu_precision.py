@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import rk_inputs
+from _parity import assert_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -84,7 +85,7 @@ def test_rkab_on_stored_rows_matches_oracle(rk, kind, m, n, q, alpha, rounds):
     assert info.status == 0
     xo = oracle.rkab(low, s.b.astype(np.float64), np.zeros(n), q=q, alpha=alpha, rounds=rounds,
                      seed=5, tab=tab)
-    assert _rel(x.cpu().numpy(), xo) < TOL
+    assert_close(x.cpu().numpy(), xo, TOL)
 
 
 @pytest.mark.parametrize("kind", ["bf16", "fp8", "f32"])
@@ -104,7 +105,7 @@ def test_refinement_steps_match_oracle(rk, kind):
     for k in range(3):
         x, info = rk.rkab_refine(plan, A, b, q=6, alpha=100, inner_rounds=4, max_outer=k + 1, seed=2)
         assert info.outer_done == k + 1
-        assert _rel(x.cpu().numpy(), xs_o[k]) < TOL, (kind, k)
+        assert_close(x.cpu().numpy(), xs_o[k], TOL, what=str((kind, k)))
 
 
 @pytest.mark.parametrize("kind", ["bf16", "fp8"])

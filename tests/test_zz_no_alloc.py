@@ -12,7 +12,9 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import rk_inputs
+from _parity import assert_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -100,3 +102,89 @@ def test_noalloc_refuses_what_does_not_fit(env):
     assert rc == _lib.RK_ETOOLARGE
     assert "fixed scratch" in L.rk_strerror(rc).decode()
     assert torch.count_nonzero(x) == 0 and torch.count_nonzero(res) == 0
+
+
+def test_noalloc_matches_oracle(env):
+    """Independent of the path it mirrors: the allocation-free solve against the FP64
+    oracle on the same draws (x within the parity tolerance, every element)."""
+    rk, _lib, L, plan, b, xs = env
+    s = rk_inputs.gaussian_system(6000, 300, seed=31)
+    x0 = torch.zeros(300, device="cuda")
+    for call in range(2):
+        x = torch.full((300,), float("nan"), device="cuda")
+        res = torch.zeros(24, dtype=torch.uint8, device="cuda")
+        assert _noalloc(L, plan, b, x0, x, 6, 40, 5, 21, rk.make_opts(check_every=0), res) == 0
+        torch.cuda.synchronize()
+        assert _result(res).status == 0
+        xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(300), q=6, alpha=40, rounds=5,
+                         seed=21, tab=oracle.table(s.A))
+        assert_close(x.cpu().numpy(), xo, TOL, what=f"call {call}")
+
+
+@pytest.mark.parametrize("case", ["cluster2", "rka_spread", "rounds0"])
+def test_noalloc_paths_match_workspace_solve(env, case):
+    """The launch shapes rkab_solve offers, through the fixed array: 2-CTA cluster
+    workers, RKA with the workers spread over one CTA per SM, and rounds = 0 (x = x0)."""
+    rk, _lib, L, plan, b, xs = env
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    q, alpha, rounds, kw = {"cluster2": (3, 25, 4, {"cluster_size": 2}),
+                            "rka_spread": (4 * sms + 3, 1, 6, {}),
+                            "rounds0": (2, 5, 0, {})}[case]
+    x0 = torch.randn(300, device="cuda")
+    ref, info = rk.rkab_solve(plan, b, x0, q=q, alpha=alpha, rounds=rounds, seed=9,
+                              check_every=0, **kw)
+    for _ in range(2):
+        x = torch.full((300,), float("nan"), device="cuda")
+        res = torch.zeros(24, dtype=torch.uint8, device="cuda")
+        rc = _noalloc(L, plan, b, x0, x, q, alpha, rounds, 9, rk.make_opts(check_every=0, **kw), res)
+        assert rc == _lib.RK_OK, L.rk_strerror(rc).decode()
+        torch.cuda.synchronize()
+        r = _result(res)
+        assert r.status == 0 and r.rounds_done == rounds
+        if rounds == 0:
+            assert torch.equal(x, x0)
+        else:
+            assert_close(x.cpu().numpy(), ref.cpu().numpy(), TOL, what=case)
+
+
+def test_noalloc_result_in_pinned_host_memory(env):
+    rk, _lib, L, plan, b, xs = env
+    x0 = torch.zeros(300, device="cuda")
+    ref, info = rk.rkab_solve(plan, b, x0, q=4, alpha=30, rounds=500, seed=5, x_ref=xs, tol=1e-5)
+    res = torch.zeros(24, dtype=torch.uint8).pin_memory()
+    x = torch.empty(300, device="cuda")
+    assert _noalloc(L, plan, b, x0, x, 4, 30, 500, 5, rk.make_opts(x_ref=xs, tol=1e-5), res) == 0
+    torch.cuda.synchronize()
+    r = Result.from_buffer_copy(res.numpy().tobytes())
+    assert r.status == 0 and r.rounds_done == info.rounds_done and 0 <= r.last_metric < 1e-5
+    assert torch.equal(x, ref)
+
+
+def test_noalloc_checks_options_like_rkab_solve(env):
+    rk, _lib, L, plan, b, xs = env
+    x0 = torch.zeros(300, device="cuda")
+    x = torch.zeros(300, device="cuda")
+    res = torch.zeros(24, dtype=torch.uint8, device="cuda")
+    for kw in ({"cluster_size": 3}, {"cluster_size": 32}, {"lookahead": 3}, {"omega": 9.0}):
+        assert _noalloc(L, plan, b, x0, x, 4, 10, 1, 0, rk.make_opts(**kw), res) == _lib.RK_EINVAL, kw
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(x) == 0 and torch.count_nonzero(res) == 0
+
+
+def test_noalloc_sizes_rka_by_the_rows_it_uses(env):
+    """RKA with more workers than SMs keeps one row of displacements per SM, so it fits
+    the array at sizes where RKAB with as many workers does not (10000 columns: 608 RKA
+    workers fit, RKAB with 608 workers of alpha = 2 is refused)."""
+    rk, _lib, L, _, _, _ = env
+    A_t, b_t, _ = rk_inputs.gaussian_system_torch(3000, 10000, seed=6, device="cuda")
+    big = rk.rk_setup(A_t)
+    q = 4 * torch.cuda.get_device_properties(0).multi_processor_count
+    x0 = torch.zeros(10000, device="cuda")
+    ref, _ = rk.rka_solve(big, b_t, x0, q=q, rounds=3, seed=2, check_every=0)
+    x = torch.full((10000,), float("nan"), device="cuda")
+    res = torch.zeros(24, dtype=torch.uint8, device="cuda")
+    assert _noalloc(L, big, b_t, x0, x, q, 1, 3, 2, rk.make_opts(check_every=0), res) == 0
+    torch.cuda.synchronize()
+    assert _result(res).status == 0
+    assert_close(x.cpu().numpy(), ref.cpu().numpy(), TOL)
+    assert _noalloc(L, big, b_t, x0, x, q, 2, 1, 2, rk.make_opts(), res) == _lib.RK_ETOOLARGE
