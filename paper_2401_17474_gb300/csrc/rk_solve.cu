@@ -31,16 +31,32 @@ __global__ void sample_indices_kernel(const uint64_t* __restrict__ thr64,
 // shared memory: half the warps of a 512-thread CTA to reduce each dot over), else
 // 512; then the smallest instantiated slices-per-thread count that covers n.
 static const SolveVariant* find_variant(const SolveVariant* tab, int count, int nt, int n4, int w,
-                                        int minb, bool jac) {
+                                        int minb, bool jac, bool xs = false) {
     const int need = (n4 + nt - 1) / nt;
     const SolveVariant* best = nullptr;
     for (int i = 0; i < count; ++i) {
-        if (tab[i].minb == minb && tab[i].jac == jac && tab[i].nt == nt && tab[i].w == w && tab[i].vpt >= need &&
-            (!best || tab[i].vpt < best->vpt))
+        if (tab[i].minb == minb && tab[i].jac == jac && tab[i].xs == xs && tab[i].nt == nt && tab[i].w == w &&
+            tab[i].vpt >= need && (!best || tab[i].vpt < best->vpt))
             best = &tab[i];
     }
     return best;
 }
+
+// Stored types whose rows of 10K-16K columns run the variant with x in shared memory
+// (bit 1 << dtype): FP8 rows, whose decoding makes the consumers the bound, gain from
+// the single pass over each row with the decoded row kept in registers (measured at
+// 100000 x 16000, q = 132: 12.7 against 16.1 ms a round); BF16 rows (13.3 against
+// 13.1 ms) and float32 rows (18.9 against 18.2 ms) do not.
+#ifndef RK_SOLVE_XS_DTYPES
+#define RK_SOLVE_XS_DTYPES 4
+#endif
+// Consumer threads of one-CTA workers on rows of 10K-16K columns: 256 (eight warps, 168
+// registers a thread), or 384 / 480 (twelve / fifteen warps and the producer's: at most
+// four warps an SM sub-partition, 128 registers a thread), whose extra warps hide more of
+// the latency of each row's dependent chain.
+#ifndef RK_SOLVE_WIDE_NT
+#define RK_SOLVE_WIDE_NT 256
+#endif
 
 static const SolveVariant* pick_variant(rk_dtype dt, int n4, int w, int minb = 1, bool jac = false) {
     int count = 0;
@@ -51,13 +67,22 @@ static const SolveVariant* pick_variant(rk_dtype dt, int n4, int w, int minb = 1
     // two workers per SM: 128 or 256 consumers, slices re-read from shared memory
     if (minb == 2) nt = n4 <= 128 * 5 ? 128 : 256;
     if (nt == 512 && n4 <= 256 * 16) {
-        const SolveVariant* v = find_variant(tab, count, 256, n4, w, minb, jac);
-        if (v) return v;
+        for (int wnt : {RK_SOLVE_WIDE_NT, 256}) {
+            if (w == 1 && minb == 1 && !jac && ((RK_SOLVE_XS_DTYPES >> (int)dt) & 1)) {
+                const SolveVariant* v = find_variant(tab, count, wnt, n4, w, minb, jac, true);
+                if (v) return v;
+            }
+            const SolveVariant* v = find_variant(tab, count, wnt, n4, w, minb, jac);
+            if (v) return v;
+        }
     }
     return find_variant(tab, count, nt, n4, w, minb, jac);
 }
 
 static const int kMaxStages = 16;
+
+// Shared memory of a variant's x (NT * VPT float4) when it keeps x there.
+static size_t xs_bytes(const SolveVariant* v) { return v->xs ? (size_t)v->nt * v->vpt * 16 : 0; }
 
 static int stages_for(uint32_t stride, int nt, int smem_max) {
     int S = 0;
@@ -257,13 +282,13 @@ int launch_solve(const SolveArgs& a, cudaStream_t st) {
         // stages are padded to the variant's NT * VPT slices (zeroed at kernel start)
         const uint32_t padded = (uint32_t)var->nt * (uint32_t)var->vpt * 4u * (uint32_t)elem_size(pl->dt);
         stride = ((row_bytes > padded ? row_bytes : padded) + 127u) & ~127u;
-        S = stages_for(stride, var->nt, smem_max);
+        S = stages_for(stride, var->nt, smem_max - (int)xs_bytes(var));
         if (S >= 2 * var->w) break;
         w = var->w > 1 ? var->w / 2 : 1;   // fewer rows per group when the ring is short
         var = nullptr;
     }
     if (!var || S < 2) return RK_EINVAL;
-    const size_t smem = (size_t)S * stride + solve_ctrl_bytes(S, var->nt);
+    const size_t smem = (size_t)S * stride + xs_bytes(var) + solve_ctrl_bytes(S, var->nt);
 
     KParams p = base_params(a);
     p.stages = S;

@@ -6,6 +6,7 @@ namespace rk {
 #define V_(NT, VPT, KA, W) SolveVariant{NT, VPT, KA, W, rkab_kernel<NT, VPT, ELT_BF16, KA, W>, 1, false}
 #define VJ_(NT, VPT, KA) SolveVariant{NT, VPT, KA, 1, rkab_kernel<NT, VPT, ELT_BF16, KA, 1, 1, true>, 1, true}
 #define V2_(NT, VPT) SolveVariant{NT, VPT, false, 1, rkab_kernel<NT, VPT, ELT_BF16, false, 1, 2>, 2, false}
+#define VX_(NT, VPT) SolveVariant{NT, VPT, true, 1, rkab_kernel<NT, VPT, ELT_BF16, true, 1, 1, false, true>, 1, false, true}
 static const SolveVariant kTab[] = {
     V_(32, 1, true, 1),    V_(32, 2, true, 1),    V_(32, 4, true, 1),
     V_(128, 2, true, 1),   V_(128, 3, true, 1),   V_(128, 5, true, 1),
@@ -25,9 +26,13 @@ static const SolveVariant kTab[] = {
     VJ_(256, 3, true),  VJ_(256, 4, true),  VJ_(256, 5, true),  VJ_(256, 6, true),
     VJ_(256, 8, true),  VJ_(256, 10, true),
     VJ_(512, 6, false), VJ_(512, 8, false), VJ_(512, 10, false),
+    VX_(256, 12), VX_(256, 16),
+    V_(384, 8, false, 1), V_(384, 11, false, 1), V_(480, 7, false, 1), V_(480, 9, false, 1),
+    VX_(384, 8), VX_(384, 11), VX_(480, 7), VX_(480, 9),
 };
 #undef V_
 #undef V2_
+#undef VX_
 #undef VJ_
 
 const SolveVariant* solve_variants_bf16(int* count) {

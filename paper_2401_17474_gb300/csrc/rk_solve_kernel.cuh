@@ -523,16 +523,22 @@ struct GroupIdx {
 // grid hold two workers per SM (more workers per round, smaller per-CTA share).
 // JAC = the CTA sums independent single projections from the round's x (RKA with
 // the workers spread over the CTAs, KParams::jacobi); W = 1 only.
-template <int NT, int VPT, int ELT, bool KEEP_A, int W, int MINB = 1, bool JAC = false>
+template <int NT, int VPT, int ELT, bool KEEP_A, int W, int MINB = 1, bool JAC = false, bool XS = false>
 __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
     static_assert(!JAC || W == 1, "independent projections are not grouped");
     static_assert(W == 1 || !KEEP_A, "look-ahead groups re-read their rows");
+    static_assert(!XS || (KEEP_A && W == 1), "x in shared memory only with the fused pass");
     static_assert(GroupIdx<W>::NV <= kRedSlots, "too many partial sums per group");
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr int NW = NT / 32;
     const int S = p.stages;
     uint8_t* stages = smem;
-    float4* avg = reinterpret_cast<float4*>(smem + (size_t)S * p.stage_stride);  // [NT]
+    // XS: the round's start point x lives in shared memory after the stages, each
+    // thread's slices at the same indices as in registers (only that thread reads
+    // and writes them, so no barrier guards them); the registers it frees hold the
+    // widened row between the dot and the update
+    float4* xs = reinterpret_cast<float4*>(smem + (size_t)S * p.stage_stride);  // [NT * VPT] if XS
+    float4* avg = xs + (XS ? NT * VPT : 0);                                     // [NT]
     uint64_t* full = reinterpret_cast<uint64_t*>(avg + NT);
     uint64_t* empty = full + S;
     float4* meta = reinterpret_cast<float4*>(empty + S);
@@ -596,7 +602,8 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
             if (j + 2 < p.n) t.z = __ldg(p.x0 + j + 2);
             if (j + 3 < p.n) t.w = __ldg(p.x0 + j + 3);
         }
-        v[k] = t;
+        if constexpr (XS) xs[idx] = t;
+        else v[k] = t;
         d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
@@ -737,13 +744,14 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
 #define RK_FUSED_SLICE(LOADEXPR)                                                        \
             {                                                                           \
                 const float4 ak = LOADEXPR;                                             \
+                const float4 xk = XS ? xs[tid + k * NT] : v[k];                         \
                 const float2 dlo = __ffma2_rn(cc, make_float2(a[k].x, a[k].y),          \
                                               make_float2(d[k].x, d[k].y));             \
                 const float2 dhi = __ffma2_rn(cc, make_float2(a[k].z, a[k].w),          \
                                               make_float2(d[k].z, d[k].w));             \
                 const float2 alo = make_float2(ak.x, ak.y), ahi = make_float2(ak.z, ak.w); \
-                p01 = __ffma2_rn(alo, make_float2(v[k].x, v[k].y), p01);                \
-                p23 = __ffma2_rn(ahi, make_float2(v[k].z, v[k].w), p23);                \
+                p01 = __ffma2_rn(alo, make_float2(xk.x, xk.y), p01);                    \
+                p23 = __ffma2_rn(ahi, make_float2(xk.z, xk.w), p23);                    \
                 if (!jac) {                                                             \
                     p01 = __ffma2_rn(alo, dlo, p01);                                    \
                     p23 = __ffma2_rn(ahi, dhi, p23);                                    \
@@ -800,19 +808,28 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
             // combined in a fixed order
             float2 p01 = make_float2(0.f, 0.f), p23 = make_float2(0.f, 0.f);
             float4 a[KEEP_A ? VPT : 1];
-#pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-                const int idx = tid + k * NT;
-                const float4 ak = slice<ELT>(stg, idx, k, tail_k, rem);
-                if constexpr (KEEP_A) a[k] = ak;
-                const float2 alo = make_float2(ak.x, ak.y), ahi = make_float2(ak.z, ak.w);
-                p01 = __ffma2_rn(alo, make_float2(v[k].x, v[k].y), p01);
-                p23 = __ffma2_rn(ahi, make_float2(v[k].z, v[k].w), p23);
-                if (!jac) {
-                    p01 = __ffma2_rn(alo, make_float2(d[k].x, d[k].y), p01);
-                    p23 = __ffma2_rn(ahi, make_float2(d[k].z, d[k].w), p23);
-                }
+            // the tail mask only when n is not a multiple of 4 (a uniform branch: the
+            // loop without it has no per-slice compare and selects)
+#define RK_DOT_LOOP(LOADEXPR)                                                           \
+            _Pragma("unroll")                                                           \
+            for (int k = 0; k < VPT; ++k) {                                             \
+                const int idx = tid + k * NT;                                           \
+                const float4 ak = LOADEXPR;                                             \
+                if constexpr (KEEP_A) a[k] = ak;                                        \
+                const float2 alo = make_float2(ak.x, ak.y), ahi = make_float2(ak.z, ak.w); \
+                p01 = __ffma2_rn(alo, make_float2(v[k].x, v[k].y), p01);                \
+                p23 = __ffma2_rn(ahi, make_float2(v[k].z, v[k].w), p23);                \
+                if (!jac) {                                                             \
+                    p01 = __ffma2_rn(alo, make_float2(d[k].x, d[k].y), p01);            \
+                    p23 = __ffma2_rn(ahi, make_float2(d[k].z, d[k].w), p23);            \
+                }                                                                       \
             }
+            if (rem == 0) {
+                RK_DOT_LOOP(load4<ELT>(stg, idx))
+            } else {
+                RK_DOT_LOOP(slice<ELT>(stg, idx, k, tail_k, rem))
+            }
+#undef RK_DOT_LOOP
             if constexpr (KEEP_A) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
@@ -834,19 +851,24 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
             // A_i = s_i q_i: <A_i, v> = s_i <q_i, v>, d += (scale s_i) q_i
             const float scale = p.omega * (mb.x - mb.z * dot) * mb.y * mb.z;
             const float2 sc2 = make_float2(scale, scale);
-#pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-                float4 ak;
-                if constexpr (KEEP_A) {
-                    ak = a[k];
-                } else {
-                    const int idx = tid + k * NT;
-                    ak = slice<ELT>(stg, idx, k, tail_k, rem);
-                }
-                const float2 dlo = __ffma2_rn(sc2, make_float2(ak.x, ak.y), make_float2(d[k].x, d[k].y));
-                const float2 dhi = __ffma2_rn(sc2, make_float2(ak.z, ak.w), make_float2(d[k].z, d[k].w));
-                d[k] = make_float4(dlo.x, dlo.y, dhi.x, dhi.y);
+#define RK_UPD_LOOP(LOADEXPR)                                                           \
+            _Pragma("unroll")                                                           \
+            for (int k = 0; k < VPT; ++k) {                                             \
+                const int idx = tid + k * NT;                                           \
+                (void)idx;                                                              \
+                float4 ak;                                                              \
+                if constexpr (KEEP_A) ak = a[k];                                        \
+                else ak = LOADEXPR;                                                     \
+                const float2 dlo = __ffma2_rn(sc2, make_float2(ak.x, ak.y), make_float2(d[k].x, d[k].y)); \
+                const float2 dhi = __ffma2_rn(sc2, make_float2(ak.z, ak.w), make_float2(d[k].z, d[k].w)); \
+                d[k] = make_float4(dlo.x, dlo.y, dhi.x, dhi.y);                         \
             }
+            if (rem == 0) {
+                RK_UPD_LOOP(load4<ELT>(stg, idx))
+            } else {
+                RK_UPD_LOOP(slice<ELT>(stg, idx, k, tail_k, rem))
+            }
+#undef RK_UPD_LOOP
             if constexpr (!KEEP_A) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
@@ -884,7 +906,9 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
             const int idx = tid + k * NT;
-            v[k] = (idx < n4) ? ldcg4(p.xbuf + (size_t)idx * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 xn = (idx < n4) ? ldcg4(p.xbuf + (size_t)idx * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (XS) xs[idx] = xn;
+            else v[k] = xn;
             d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
 
@@ -926,6 +950,7 @@ struct SolveVariant {
     SolveKernelFn fn;
     int minb;           // CTAs per SM the register budget allows (1 or 2)
     bool jac;           // independent projections from the round's x (RKA spread over CTAs)
+    bool xs;            // x in shared memory (NT * VPT float4 after the stages)
 };
 
 // Instantiation tables (one translation unit per stored type).

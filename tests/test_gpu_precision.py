@@ -73,7 +73,10 @@ def test_stored_row_tables_bit_exact(rk, sysm, kind, shape):
 
 @pytest.mark.parametrize("kind", ["bf16", "fp8"])
 @pytest.mark.parametrize("m,n,q,alpha,rounds", [(3001, 37, 3, 7, 10), (6000, 2600, 5, 30, 3),
-                                                (2500, 300, 8, 40, 6), (2000, 15000, 2, 15, 2)])
+                                                (2500, 300, 8, 40, 6), (2000, 15000, 2, 15, 2),
+                                                # x in shared memory: 16 slices a thread with a ragged
+                                                # tail, and 12 slices a thread
+                                                (1500, 15003, 3, 20, 2), (2500, 11001, 4, 25, 3)])
 def test_rkab_on_stored_rows_matches_oracle(rk, kind, m, n, q, alpha, rounds):
     s = rk_inputs.gaussian_system(m, n, seed=m + 2 * n)
     A = rk.aligned_rows(_dev(s.A))
