@@ -75,14 +75,17 @@ def parse():
                     help="relaxation of the timed solve: a number, or 'star' for alpha* of "
                          "Eq. (best_alpha) from the GPU spectrum estimate (computed before timing)")
     ap.add_argument("--workload", default="consistent",
-                    choices=["consistent", "lsq", "precision", "horizon", "adjoint", "setup"],
+                    choices=["consistent", "lsq", "precision", "horizon", "adjoint", "adjoint-c5",
+                             "setup", "rounds"],
                     help="consistent: 80000 x 10000 to 1e-6 (default); lsq: 200000 x 20000 "
                          "row-scaled inconsistent system, budget of rounds with the normal-equation "
                          "criterion logged every round; precision: 1e6 x 16000, FP32 vs BF16/FP8 "
                          "+ refinement to 1e-6; horizon: 80000 x 1000 inconsistent system, error "
                          "to x_LS and residual along RKA / RKAB runs for several worker counts; "
                          "adjoint: backward pass of the least-squares solve at 200000 x 20000; "
-                         "setup: rk_setup alone on --m x --n stored as --dtype")
+                         "adjoint-c5: the differentiation workload at 50000 x 5000 with its "
+                         "gradient errors; setup: rk_setup alone on --m x --n stored as --dtype; "
+                         "rounds: one RKAB round per storage (consumer speed)")
     return ap.parse_args()
 
 
@@ -391,6 +394,31 @@ def extra_precision(rk, A, plan32, b, xs, n, q, alpha, tol):
                                          bytes_per_row=n * {"bf16": 2, "fp8": 1}[kind])
         except Exception as e:
             out[f"{kind}_refine"] = {"error": str(e)}
+    out["round_ms"] = round_times(rk, A, plan32, b, n, q, alpha)
+    return out
+
+
+def round_times(rk, A, plan32, b, n, q, alpha, rounds=2):
+    """One RKAB round (q workers, alpha projections each, no checks) on FP32, BF16 and FP8
+    rows: the consumers' speed on each storage (ms a round, and microseconds a row per
+    worker)."""
+    import torch
+    x0 = torch.zeros(n, dtype=torch.float32, device=b.device)
+    x = torch.empty_like(x0)
+    out = {}
+    for kind in ("f32", "bf16", "fp8"):
+        if kind == "f32":
+            pl, keep = plan32, None
+        else:
+            Aq, sc = rk.quantize(A, kind)
+            pl, keep = rk.rk_setup(Aq, kind, sc), (Aq, sc)
+        s = rk.Solver(pl, q)
+        o = rk.make_opts(check_every=0)
+        t = _timed(lambda: s.launch(b, x0, x, alpha, rounds, 0, o), reps=2) / rounds
+        out[kind] = {"ms": round(t, 3), "us_per_row": round(1e3 * t / alpha, 4),
+                     "GBps": round(q * alpha * n * {"f32": 4, "bf16": 2, "fp8": 1}[kind] / (t / 1e3) / 1e9, 1)}
+        del s, pl, keep
+    torch.cuda.empty_cache()
     return out
 
 
@@ -528,34 +556,159 @@ def extra_sampling(rk, A, plan, b, xs, n, tol):
     return out
 
 
-def extra_adjoint(rk, dev, seed):
-    """Backward pass of the differentiation workload 50000 x 5000 (b = A x* + N(0, 1e-3^2),
-    L = 0.5 ||x - x_t||^2): A^T copy and plan, minimum-norm solve on A^T (16-CTA clusters),
-    solve of A g = y, residual, rank-2 gradient of A."""
+class LsqReference:
+    """FP64 least-squares references on the GPU for the differentiation workload (a
+    measurement reference, not the method): the Cholesky factor of A^T A (kappa(A) ~ 2
+    here, so the normal equations lose nothing in FP64), x_LS with two refinement steps
+    on the true residual, the exact adjoint of L = 0.5 ||x - x_t||^2 at any point, and
+    central finite differences of the exact map L(x_LS(A, b))."""
+
+    def __init__(self, A, b):
+        import torch
+        self.A = A.double()
+        self.b = b.double()
+        self.L = torch.linalg.cholesky(self.A.T @ self.A)
+        self.x_ls = self.solve(self.A.T @ self.b)
+        for _ in range(2):
+            self.x_ls = self.x_ls + self.solve(self.A.T @ (self.b - self.A @ self.x_ls))
+
+    def solve(self, v):
+        import torch
+        return torch.cholesky_solve(v.unsqueeze(1), self.L).squeeze(1)
+
+    def adjoint(self, x, xt):
+        """(grad_A, grad_b) of 0.5 ||x - x_t||^2 through x = argmin ||A x - b|| at the point x:
+        g = (A^T A)^{-1} (x - x_t), y = A g, grad_b = y, grad_A = r g^T - y x^T."""
+        import torch
+        x = x.double()
+        g = self.solve(x - xt.double())
+        y = self.A @ g
+        r = self.b - self.A @ x
+        return torch.outer(r, g) - torch.outer(y, x), y
+
+    def _delta(self, dA, db, h, steps=4):
+        """x_LS(A + h dA, b + h db) - x_LS(A, b): the perturbed normal equations solved by
+        preconditioned Richardson steps with the Cholesky factor of A^T A (the preconditioned
+        operator is I + O(h ||dA|| / ||A||), so each step gains about six digits)."""
+        A, x0 = self.A, self.x_ls
+
+        def mv(v):
+            u = A @ v + h * (dA @ v)
+            return A.T @ u + h * (dA.T @ u)
+
+        r_h = (self.b + h * db) - (A @ x0 + h * (dA @ x0))
+        rhs = A.T @ r_h + h * (dA.T @ r_h)
+        d = self.solve(rhs)
+        for _ in range(steps):
+            d = d + self.solve(rhs - mv(d))
+        return d
+
+    def fd_check(self, gA, gb, xt, directions=32, h=1e-6, seed=1):
+        """Worst relative gap over random directions (dA, db) ~ N(0,1) between the central
+        difference (L(h) - L(-h)) / 2h of the exact map and <gA, dA> + <gb, db>; the
+        difference of the two losses is formed as <x_LS - x_t, d+ - d-> +
+        0.5 (||d+||^2 - ||d-||^2) with d+- the perturbations of x_LS (the same value, without
+        the cancellation of two losses of order 1e3)."""
+        import torch
+        gen = torch.Generator(device=self.A.device).manual_seed(seed)
+        gA64, gb64 = gA.double(), gb.double()
+        e = self.x_ls - xt.double()
+        fds, ans = [], []
+        for _ in range(directions):
+            dA = torch.randn(self.A.shape, dtype=torch.float64, device=self.A.device, generator=gen)
+            db = torch.randn(self.b.shape, dtype=torch.float64, device=self.A.device, generator=gen)
+            dp, dm = self._delta(dA, db, h), self._delta(dA, db, -h)
+            fds.append((float(e @ (dp - dm)) + 0.5 * (float(dp @ dp) - float(dm @ dm))) / (2 * h))
+            ans.append(float((gA64 * dA).sum()) + float(gb64 @ db))
+            del dA
+        import numpy as np
+        fd, an = np.array(fds), np.array(ans)
+        # per direction the relative gap is a ratio of two nearly independent Gaussians
+        # (the gradient error and the gradient, each projected on a random direction), so
+        # its maximum over 32 directions is heavy-tailed; the relative L2 gap of the 32
+        # directional derivatives is the stable figure
+        return {"fd_rel_err_32_directions": float(np.linalg.norm(fd - an) / np.linalg.norm(fd)),
+                "fd_worst_rel_err_32_directions": float(np.max(np.abs(fd - an) / np.abs(fd))),
+                "fd_smallest_over_rms": float(np.min(np.abs(fd)) / np.sqrt(np.mean(fd ** 2)))}
+
+
+def _rel64(a, b):
+    return float((a.double() - b.double()).norm() / b.double().norm())
+
+
+def adjoint_c5(rk, dev, seed, sched_fracs=((1.0, 100), (0.1, 300), (0.01, 1500)),
+               rounds_t=24, omega_t=1.0, rounds_g=200, check=True, q_t=6, cluster_t=16, alpha_t=0):
+    """The differentiation workload at 50000 x 5000 (b = A x* + N(0, 1e-3^2), x_t ~ N(0,1),
+    L = 0.5 ||x - x_t||^2) through torch.autograd: the forward RKA solve with 32 workers per
+    SM and a decreasing relaxation (alpha* of Eq. (best_alpha), then a tenth, ...: the
+    horizon shrinks with the weight), the backward pass (A^T copy and plan, minimum-norm
+    solve on A^T by 16-CTA cluster workers, RKA solve of A g = y, residual, rank-2 gradient).
+    Reported beside the times: ||x - x_LS|| / ||x_LS||, the gradient against the FP64 adjoint
+    at x_LS and at the GPU's x, and the worst of 32 central finite differences (step 1e-6)
+    of the FP64 map L(x_LS(A, b))."""
     import torch
 
     import rk_inputs
     m, n = 50000, 5000
-    A, b, xs = rk_inputs.gaussian_system_torch(m, n, seed=seed + 7, noise=1e-3, device=str(dev))
+    A, b, _ = rk_inputs.gaussian_system_torch(m, n, seed=seed + 7, noise=1e-3, device=str(dev))
     xt = torch.randn(n, generator=torch.Generator(device=dev).manual_seed(5), device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    qa = 32 * sms
     plan = rk.rk_setup(A)
-    x, _ = rk.rkab_solve(plan, b, q=16, alpha=n, rounds=30, seed=seed, check_every=0)
-    cfg = rk.AdjointConfig(q=6, alpha_t=n, rounds_t=30, alpha=n, rounds=30, seed=seed + 1,
-                           cluster_size_t=16)
+    w, _ = rk.optimal_weight(A, qa, k=2, plan=plan)
+    sched = tuple((w * f, r) for f, r in sched_fracs)
+    alpha_t = alpha_t or n
+    cfg = rk.AdjointConfig(q=qa, alpha=1, rounds=rounds_g, omega=w, q_t=q_t, cluster_size_t=cluster_t,
+                           alpha_t=alpha_t, rounds_t=rounds_t, omega_t=omega_t, seed=seed + 1)
+    Ar = A.clone().requires_grad_(True)
+    br = b.clone().requires_grad_(True)
+    torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    adj = rk.Adjoint(plan, cfg)
-    torch.cuda.synchronize()
-    t_setup = (time.perf_counter() - t0) * 1e3
-    gx = x - xt
-    t = _timed(lambda: adj.backward(b, x, gx), reps=2)
-    return {"workload": f"lstsq_adjoint_{m}x{n}", "backward_ms": round(t, 2),
-            "transpose_and_plan_ms": round(t_setup, 2), "q": 6, "rounds_t": 30, "rounds_g": 30,
-            "grad_A_bytes": m * n * 4}
+    x = rk.rkab_lstsq(Ar, br, q=qa, alpha=1, seed=seed, adjoint=cfg, schedule=sched)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    loss = 0.5 * ((x - xt) ** 2).sum()
+    gA, gb = torch.autograd.grad(loss, (Ar, br))
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    out = {"workload": f"lstsq_adjoint_{m}x{n}", "forward_ms": round((t1 - t0) * 1e3, 2),
+           "backward_ms": round((t2 - t1) * 1e3, 2),
+           "forward": f"RKA q={qa}, weights alpha* x " + ", ".join(f"{f:g} ({r} rounds)" for f, r in sched_fracs),
+           "y_solve": f"RKAB on A^T, {q_t} workers of {cluster_t}-CTA clusters, alpha={alpha_t}, {rounds_t} rounds, "
+                      f"omega={omega_t:g}",
+           "g_solve": f"RKA q={qa}, alpha*, {rounds_g} rounds", "grad_A_bytes": m * n * 4}
+    if check:
+        xd = x.detach()
+        ref = LsqReference(A, b)
+        gA_ls, gb_ls = ref.adjoint(ref.x_ls, xt)
+        gA_x, gb_x = ref.adjoint(xd, xt)
+        out.update({
+            "x_rel_err_vs_x_ls": _rel64(xd, ref.x_ls),
+            "grad_A_rel_err_vs_fp64_at_x_ls": _rel64(gA, gA_ls),
+            "grad_b_rel_err_vs_fp64_at_x_ls": _rel64(gb, gb_ls),
+            "grad_A_rel_err_vs_fp64_at_x": _rel64(gA, gA_x),
+            "grad_b_rel_err_vs_fp64_at_x": _rel64(gb, gb_x),
+            "y_solve_rel_residual": float((ref.A.T @ gb.double() - (xd - xt).double()).norm()
+                                          / (xd - xt).double().norm()),
+            **ref.fd_check(gA, gb, xt),
+            "reference": "FP64 on the GPU: Cholesky of A^T A, x_LS refined twice, exact adjoint, "
+                         "finite differences by preconditioned CG (step 1e-6)"})
+        del ref
+    return out
+
+
+def extra_adjoint(rk, dev, seed):
+    return adjoint_c5(rk, dev, seed)
 
 
 # ---------------------------------------------------------------------------
 # Other workloads of the benchmark list (each prints its own line)
 # ---------------------------------------------------------------------------
+def sms_of(dev):
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
 def _base_line(args, metric, value, unit, ms_per_step, config, clk, launches, hib=True):
     ws, _, _ = dist_env()
     return {"metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps,
@@ -625,6 +778,34 @@ def run_lsq(args, rk, dev):
     line["roofline"] = {"bound": "hbm", "achieved": alg / kmean / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": alg / kmean / 1e9 / peak, "traffic": None, "peak_kind": kind,
                         "kernel": "rkab_kernel (one CTA per worker)", "kernel_ms": 1e3 * kmean}
+    if not args.no_extras:
+        # the layout of the benchmark list (x split over a 4-CTA cluster): 132 workers of 4
+        # CTAs (528 CTAs at 288 threads and 168 registers a thread: one CTA an SM) cannot be
+        # co-resident on 152 SMs, so it runs with the most workers that fit, 38
+        qc, cc = (sms_of(dev) // 4), 4
+        sc = rk.Solver(plan, qc)
+        xa = torch.zeros(n, dtype=torch.float32, device=dev)
+        xb = torch.empty_like(xa)
+        crit_c, kern_c = [], []
+        for r in range(rounds):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sc.launch(b, xa, xb, alpha, 1, args.seed, rk.make_opts(check_every=0, round0=r, cluster_size=cc))
+            e1.record()
+            res.launch(A, b, xb, None, norms, True)
+            nr = norms.cpu().numpy()
+            crit_c.append(float(nr[1] / (fro * nr[0])))
+            kern_c.append(e0.elapsed_time(e1))
+            if sc.info().status != 0:
+                raise rk.RkError(sc.info().status, "lsq cluster round")
+            xa, xb = xb, xa
+        km = sum(kern_c[args.warmup:]) / args.steps
+        line["cluster_layout"] = {
+            "q": qc, "cluster": cc, "round_ms": km,
+            "row_proj_per_s": qc * alpha / (km / 1e3),
+            "alg_GBps": algorithmic_bytes(n, qc, alpha, 1) / (km / 1e3) / 1e9,
+            "criterion_per_round": crit_c,
+            "one_cta_workers": {"q": q, "round_ms": 1e3 * kmean, "row_proj_per_s": q * alpha / kmean}}
     return line
 
 
@@ -790,6 +971,7 @@ def run_precision(args, rk, dev):
         out[f"fp32_rka_q{qa}_alpha_star"] = {"ms": round(t, 2), "rounds": s3.info().rounds_done,
                                              "metric": s3.info().last_metric}
     out["inconsistent"] = precision_inconsistent(rk, A, plan, b, n, q, alpha, args, dev)
+    out["round_ms"] = round_times(rk, A, plan, b, n, q, alpha)
     peak, kind = load_peaks()
     line = _base_line(args, METRIC, units / (total / 1e3), UNIT, total / args.steps,
                       {"workload": f"rkab_precision_{m}x{n}_q{q}_alpha{alpha}",
@@ -802,7 +984,71 @@ def run_precision(args, rk, dev):
                         "peak": peak, "unit": "GB/s",
                         "frac": alg / (total / args.steps / 1e3) / 1e9 / peak, "traffic": None,
                         "peak_kind": kind, "kernel": "rkab_kernel (setup + solve, one step)"}
+    line["summary"] = precision_summary(out)
     return line
+
+
+def precision_summary(out):
+    """Time to tolerance of each storage, solves alone (plans and stored copies built
+    beforehand): plain FP32 against BF16 / FP8 rows with refinement, and their ratios."""
+    f = out.get("fp32_plain", {})
+    f_ms = f.get("solve_ms", f.get("ms"))
+    res = {"fp32_plain_ms": f_ms}
+    for kind in ("bf16", "fp8"):
+        r = out.get(f"{kind}_refine", {})
+        ms = r.get("ms")
+        res[f"{kind}_refine_ms"] = ms
+        res[f"{kind}_refine_over_fp32_plain"] = round(ms / f_ms, 4) if ms and f_ms else None
+        res[f"{kind}_refine_reached_tol"] = r.get("metric") is not None and 0 <= r.get("metric", -1) < 1e-6
+    rt = out.get("round_ms") or {}
+    for kind in ("f32", "bf16", "fp8"):
+        if kind in rt:
+            res[f"{kind}_round_ms"] = rt[kind]["ms"]
+    return res
+
+
+def run_rounds(args, rk, dev):
+    """Consumer speed per storage: one RKAB round (q workers, alpha projections each, no
+    checks) on float32, BF16 and FP8 rows of an m x n Gaussian system (defaults 100000 x
+    16000, q = 132, alpha = n), timed --steps times after one untimed launch; --dtype
+    picks one storage (f32: all three)."""
+    import torch
+
+    import rk_inputs
+    m = args.m if args.m != 80000 else 100000
+    n = args.n if args.n != 10000 else 16000
+    q, alpha = args.q, args.alpha or n
+    A, b, _ = rk_inputs.gaussian_system_torch(m, n, seed=args.seed, device=str(dev))
+    plan = rk.rk_setup(A)
+    x0 = torch.zeros(n, dtype=torch.float32, device=dev)
+    x = torch.empty_like(x0)
+    kinds = ("f32", "bf16", "fp8") if args.dtype == "f32" else (args.dtype,)
+    out = {}
+    for kind in kinds:
+        if kind == "f32":
+            pl, keep = plan, None
+        else:
+            Aq, sc = rk.quantize(A, kind)
+            pl, keep = rk.rk_setup(Aq, kind, sc), (Aq, sc)
+        s = rk.Solver(pl, q)
+        o = rk.make_opts(check_every=0)
+        s.launch(b, x0, x, alpha, 1, 0, o)
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.launch(b, x0, x, alpha, 1, 0, o)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        t = sum(ts) / len(ts)
+        eb = {"f32": 4, "bf16": 2, "fp8": 1}[kind]
+        out[kind] = {"ms": round(t, 3), "us_per_row": round(1e3 * t / alpha, 4),
+                     "row_GBps": round(q * alpha * n * eb / (t / 1e3) / 1e9, 1)}
+        del s, pl, keep
+    return {"workload": f"rkab_round_{m}x{n}_q{q}_alpha{alpha}", "round": out,
+            "note": "value unused: this workload times single rounds per storage"}
 
 
 def run_horizon(args, rk, dev):
@@ -992,7 +1238,8 @@ def run_ours(args):
     if args.workload != "consistent":
         if rank == 0:
             fn = {"lsq": run_lsq, "precision": run_precision, "horizon": run_horizon,
-                  "adjoint": run_adjoint_large, "setup": run_setup}[args.workload]
+                  "adjoint": run_adjoint_large, "setup": run_setup, "rounds": run_rounds,
+                  "adjoint-c5": lambda a, r, d: adjoint_c5(r, d, a.seed)}[args.workload]
             print(json.dumps(fn(args, rk, dev)), flush=True)
         if ws > 1:
             import torch.distributed as dist
@@ -1173,6 +1420,34 @@ def run_ours(args):
                "h2d_bytes_per_step": A_h.numel() * 4 + b_h.numel() * 4 + xs_h.numel() * 4,
                "d2h_bytes_per_step": n * 4, "ms_per_step": e_ms / e2e_steps, "steps": e2e_steps,
                "pipelined": "copy of step k+1 overlaps the solve of step k (two device buffers)"}
+        # the same call unpipelined: every step copies A, b and x* in, builds the plan, solves
+        # and reads x back, all on one stream, and the host waits for x before the next step
+        A_d, b_d, xs_d = bufs[0]
+        u_ms, u_rounds = [], 0
+        for k in range(e2e_steps):
+            u0 = torch.cuda.Event(enable_timing=True)
+            u1 = torch.cuda.Event(enable_timing=True)
+            u0.record(stream)
+            with torch.cuda.stream(stream):
+                A_d.copy_(A_h, non_blocking=True)
+                b_d.copy_(b_h, non_blocking=True)
+                xs_d.copy_(xs_h, non_blocking=True)
+            pl = rk.rk_setup(A_d, stream=stream, workspace=setup_ws)
+            solver.plan = pl
+            solver.launch(b_d, x0, x, alpha, args.max_rounds, args.seed,
+                          rk.make_opts(check_every=1, tol=args.tol, x_ref=xs_d,
+                                       cluster_size=args.cluster, lookahead=args.lookahead,
+                                       omega=omega),
+                          stream)
+            with torch.cuda.stream(stream):
+                x_h.copy_(x, non_blocking=True)
+            u1.record(stream)
+            u1.synchronize()
+            u_ms.append(u0.elapsed_time(u1))
+            u_rounds += solver.info(stream).rounds_done
+        e2e["unpipelined"] = {"value": q * alpha * u_rounds / (sum(u_ms) / 1e3), "unit": UNIT,
+                              "ms_per_step": sum(u_ms) / len(u_ms), "steps": e2e_steps,
+                              "what": "one call per step: copy A, b, x* in, setup, solve, copy x out"}
         del A_h, bufs
 
     extras = {}
@@ -1218,10 +1493,28 @@ def run_ours(args):
             line["config"]["two_phase_protocol"] = protocol
         if extras:
             line["config"]["time_to_tol_cells"] = extras.get("cells")
+            line["sampling"] = extras.get("sampling")
+            line["relaxed"] = extras.get("relaxed")
             line["precision"] = extras.get("precision")
             line["adjoint"] = extras.get("adjoint")
-            line["relaxed"] = extras.get("relaxed")
-            line["sampling"] = extras.get("sampling")
+            # the headline comparisons as scalars of the workload's record, and last in the
+            # line (a reader of its tail sees them)
+            prec = extras.get("precision") or {}
+            if "fp32_plain" in prec:
+                ps = precision_summary(prec)
+                line["precision_summary"] = ps
+                for k in ("fp32_plain_ms", "bf16_refine_ms", "fp8_refine_ms",
+                          "bf16_refine_over_fp32_plain", "fp8_refine_over_fp32_plain",
+                          "f32_round_ms", "bf16_round_ms", "fp8_round_ms"):
+                    line["config"][f"precision_{k}"] = ps.get(k)
+            adj = extras.get("adjoint") or {}
+            if "fd_worst_rel_err_32_directions" in adj:
+                keys = ("forward_ms", "backward_ms", "x_rel_err_vs_x_ls", "grad_A_rel_err_vs_fp64_at_x_ls",
+                        "grad_b_rel_err_vs_fp64_at_x_ls", "fd_rel_err_32_directions",
+                        "fd_worst_rel_err_32_directions")
+                line["adjoint_summary"] = {k: adj.get(k) for k in keys}
+                for k in keys:
+                    line["config"][f"adjoint_50000x5000_{k}"] = adj.get(k)
             best = (extras.get("relaxed") or {}).get("best")
             if best:
                 line["time_to_tol_best"] = best

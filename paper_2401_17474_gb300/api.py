@@ -531,9 +531,10 @@ class Adjoint:
         g = torch.empty(n, dtype=torch.float32, device=dev)
         ldg = (n + 3) // 4 * 4
         grad_A = torch.empty((m, ldg), dtype=torch.float32, device=dev)[:, :n]
-        ot = make_opts(omega=c.omega_t, check_every=0, cluster_size=c.cluster_size_t,
+        # check_every = 1: no criterion, but a diverging solve ends with RK_EDIVERGED
+        ot = make_opts(omega=c.omega_t, check_every=1, cluster_size=c.cluster_size_t,
                        lookahead=c.lookahead)
-        oa = make_opts(omega=c.omega, check_every=0, cluster_size=c.cluster_size,
+        oa = make_opts(omega=c.omega, check_every=1, cluster_size=c.cluster_size,
                        lookahead=c.lookahead)
         check(_lib.load().rkab_adjoint(self.plan_A.handle, self.plan_At.handle, _ptr(b), _ptr(x),
                                        _ptr(gx), c.q_t or c.q, c.q, c.alpha_t or n, c.rounds_t,
