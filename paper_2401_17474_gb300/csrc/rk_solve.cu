@@ -50,13 +50,7 @@ static const SolveVariant* find_variant(const SolveVariant* tab, int count, int 
 #ifndef RK_SOLVE_XS_DTYPES
 #define RK_SOLVE_XS_DTYPES 4
 #endif
-// Consumer threads of one-CTA workers on rows of 10K-16K columns: 256 (eight warps, 168
-// registers a thread), or 384 / 480 (twelve / fifteen warps and the producer's: at most
-// four warps an SM sub-partition, 128 registers a thread), whose extra warps hide more of
-// the latency of each row's dependent chain.
-#ifndef RK_SOLVE_WIDE_NT
-#define RK_SOLVE_WIDE_NT 256
-#endif
+
 
 static const SolveVariant* pick_variant(rk_dtype dt, int n4, int w, int minb = 1, bool jac = false) {
     int count = 0;
@@ -67,14 +61,12 @@ static const SolveVariant* pick_variant(rk_dtype dt, int n4, int w, int minb = 1
     // two workers per SM: 128 or 256 consumers, slices re-read from shared memory
     if (minb == 2) nt = n4 <= 128 * 5 ? 128 : 256;
     if (nt == 512 && n4 <= 256 * 16) {
-        for (int wnt : {RK_SOLVE_WIDE_NT, 256}) {
-            if (w == 1 && minb == 1 && !jac && ((RK_SOLVE_XS_DTYPES >> (int)dt) & 1)) {
-                const SolveVariant* v = find_variant(tab, count, wnt, n4, w, minb, jac, true);
-                if (v) return v;
-            }
-            const SolveVariant* v = find_variant(tab, count, wnt, n4, w, minb, jac);
+        if (w == 1 && minb == 1 && !jac && ((RK_SOLVE_XS_DTYPES >> (int)dt) & 1)) {
+            const SolveVariant* v = find_variant(tab, count, 256, n4, w, minb, jac, true);
             if (v) return v;
         }
+        const SolveVariant* v = find_variant(tab, count, 256, n4, w, minb, jac);
+        if (v) return v;
     }
     return find_variant(tab, count, nt, n4, w, minb, jac);
 }

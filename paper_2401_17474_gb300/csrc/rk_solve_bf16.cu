@@ -27,8 +27,6 @@ static const SolveVariant kTab[] = {
     VJ_(256, 8, true),  VJ_(256, 10, true),
     VJ_(512, 6, false), VJ_(512, 8, false), VJ_(512, 10, false),
     VX_(256, 12), VX_(256, 16),
-    V_(384, 8, false, 1), V_(384, 11, false, 1), V_(480, 7, false, 1), V_(480, 9, false, 1),
-    VX_(384, 8), VX_(384, 11), VX_(480, 7), VX_(480, 9),
 };
 #undef V_
 #undef V2_

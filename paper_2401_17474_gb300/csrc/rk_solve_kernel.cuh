@@ -324,7 +324,21 @@ struct ChkAcc {
     float xx, e2, r2;
 };
 
-__device__ __forceinline__ void store_x(const KParams& p, int c, float4 xm, ChkAcc* acc) {
+// The reference solution's slice c (elements past n read as 0), loaded before the
+// column sums so that its latency overlaps theirs.
+__device__ __forceinline__ float4 load_xref(const KParams& p, int c, bool want) {
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (want && p.criterion == 1) {
+        const int j = c * 4;
+        t.x = __ldg(p.x_ref + j);
+        if (j + 1 < p.n) t.y = __ldg(p.x_ref + j + 1);
+        if (j + 2 < p.n) t.z = __ldg(p.x_ref + j + 2);
+        if (j + 3 < p.n) t.w = __ldg(p.x_ref + j + 3);
+    }
+    return t;
+}
+
+__device__ __forceinline__ void store_x(const KParams& p, int c, float4 xm, ChkAcc* acc, float4 xr4) {
     reinterpret_cast<float4*>(p.xbuf)[c] = xm;
     const int j = c * 4;
     p.x[j] = xm.x;
@@ -333,12 +347,13 @@ __device__ __forceinline__ void store_x(const KParams& p, int c, float4 xm, ChkA
     if (j + 3 < p.n) p.x[j + 3] = xm.w;
     if (acc) {
         const float vv[4] = {xm.x, xm.y, xm.z, xm.w};
+        const float rr[4] = {xr4.x, xr4.y, xr4.z, xr4.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             if (j + e < p.n) {
                 acc->xx = fmaf(vv[e], vv[e], acc->xx);
                 if (p.criterion == 1) {
-                    const float xr = __ldg(p.x_ref + j + e);
+                    const float xr = rr[e];
                     const float dd = vv[e] - xr;
                     acc->e2 = fmaf(dd, dd, acc->e2);
                     acc->r2 = fmaf(xr, xr, acc->r2);
@@ -391,9 +406,10 @@ __device__ __forceinline__ void average_slice(const KParams& p, float4* avg, boo
     if (nc >= NT) {
         for (int c = c0 + tid; c < c1; c += NT) {
             const float4 xo = load_x_old(p, c, first);
+            const float4 xr = load_xref(p, c, chk != nullptr);
             const float4 acc = sum_column<kAvgBatch>(p, c, 0, p.vrows);
             store_x(p, c, make_float4(fmaf(acc.x, rq, xo.x), fmaf(acc.y, rq, xo.y), fmaf(acc.z, rq, xo.z),
-                                      fmaf(acc.w, rq, xo.w)), chk);
+                                      fmaf(acc.w, rq, xo.w)), chk, xr);
         }
         return;
     }
@@ -401,8 +417,11 @@ __device__ __forceinline__ void average_slice(const KParams& p, float4* avg, boo
     if (groups > p.vrows) groups = p.vrows;
     const int per = (p.vrows + groups - 1) / groups;
     const int cl = tid % nc, g = tid / nc;
-    float4 xo = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (tid < nc) xo = load_x_old(p, c0 + tid, first);
+    float4 xo = make_float4(0.f, 0.f, 0.f, 0.f), xr = xo;
+    if (tid < nc) {
+        xo = load_x_old(p, c0 + tid, first);
+        xr = load_xref(p, c0 + tid, chk != nullptr);
+    }
     if (g < groups) {
         const int ga = g * per, gb = min(p.vrows, ga + per);
         avg[g * nc + cl] = sum_column<kAvgBatch>(p, c0 + cl, ga, gb);
@@ -415,16 +434,17 @@ __device__ __forceinline__ void average_slice(const KParams& p, float4* avg, boo
             acc.x += w.x; acc.y += w.y; acc.z += w.z; acc.w += w.w;
         }
         store_x(p, c0 + tid, make_float4(fmaf(acc.x, rq, xo.x), fmaf(acc.y, rq, xo.y), fmaf(acc.z, rq, xo.z),
-                                         fmaf(acc.w, rq, xo.w)), chk);
+                                         fmaf(acc.w, rq, xo.w)), chk, xr);
     }
 }
 
 // CTA sum of the threads' check partials in a fixed order (warp butterfly, then
 // warps in ascending order), published by thread 0 as this CTA's entry of
-// p.chkpart before the grid barrier that follows.
+// p.chkpart before the grid barrier that follows.  In two halves around a CTA
+// barrier the caller may already have: the warp sums into shared memory, then
+// thread 0's sum over the warps.
 template <int NT>
-__device__ __forceinline__ void publish_check(const KParams& p, ChkAcc a, double* chk) {
-    constexpr int NW = NT / 32;
+__device__ __forceinline__ void check_warp_partials(ChkAcc a, double* chk) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* sh = reinterpret_cast<float*>(chk);
 #pragma unroll
@@ -438,17 +458,27 @@ __device__ __forceinline__ void publish_check(const KParams& p, ChkAcc a, double
         sh[32 + warp] = a.e2;
         sh[64 + warp] = a.r2;
     }
-    named_bar_sync(1, NT);
-    if (threadIdx.x == 0) {
-        float xx = 0.f, e2 = 0.f, r2 = 0.f;
+}
+
+template <int NT>
+__device__ __forceinline__ void check_cta_partial(const KParams& p, const double* chk) {
+    constexpr int NW = NT / 32;
+    const float* sh = reinterpret_cast<const float*>(chk);
+    float xx = 0.f, e2 = 0.f, r2 = 0.f;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            xx += sh[w];
-            e2 += sh[32 + w];
-            r2 += sh[64 + w];
-        }
-        reinterpret_cast<float4*>(p.chkpart)[blockIdx.x] = make_float4(xx, e2, r2, 0.f);
+    for (int w = 0; w < NW; ++w) {
+        xx += sh[w];
+        e2 += sh[32 + w];
+        r2 += sh[64 + w];
     }
+    reinterpret_cast<float4*>(p.chkpart)[blockIdx.x] = make_float4(xx, e2, r2, 0.f);
+}
+
+template <int NT>
+__device__ __forceinline__ void publish_check(const KParams& p, ChkAcc a, double* chk) {
+    check_warp_partials<NT>(a, chk);
+    named_bar_sync(1, NT);
+    if (threadIdx.x == 0) check_cta_partial<NT>(p, chk);
 }
 
 // Totals of all CTAs' check partials, summed by warp 0 in a fixed order (lane l
@@ -897,8 +927,9 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
         const bool check = p.check_every > 0 && (done % p.check_every == 0 || last);
         ChkAcc ca{0.f, 0.f, 0.f};
         average_slice<NT>(p, avg, r == 0, check ? &ca : nullptr);
+        if (check) check_warp_partials<NT>(ca, chk);
         named_bar_sync(1, NT);
-        if (check) publish_check<NT>(p, ca, chk);
+        if (check && tid == 0) check_cta_partial<NT>(p, chk);
         if (tid == 0) ctrl->flag = grid_sync(&p.info->bar_arrivals, 2ull * (unsigned long long)r + 1ull,
                                              gridDim.x, status, p.timeout_ns) ? 1 : 0;
         named_bar_sync(1, NT);
