@@ -782,11 +782,22 @@ def run_lsq(args, rk, dev):
     if not args.no_extras:
         # the layout of the benchmark list (x split over a 4-CTA cluster): 132 workers of 4
         # CTAs (528 CTAs at 288 threads and 168 registers a thread: one CTA an SM) cannot be
-        # co-resident on 152 SMs, so it runs with the most workers that fit, 38
-        qc, cc = (sms_of(dev) // 4), 4
-        sc = rk.Solver(plan, qc)
+        # co-resident on 152 SMs, so it runs with the most workers that fit (at most 38; the
+        # clusters must also fit whole into the GPCs)
+        cc = 4
         xa = torch.zeros(n, dtype=torch.float32, device=dev)
         xb = torch.empty_like(xa)
+        qc = sms_of(dev) // cc
+        while True:
+            sc = rk.Solver(plan, qc)
+            try:
+                sc.launch(b, xa, xb, alpha, 1, args.seed, rk.make_opts(check_every=0, cluster_size=cc))
+                break
+            except rk.RkError as e:
+                if e.code != -3 or qc <= 1:
+                    raise
+                qc -= 1
+        torch.cuda.synchronize(dev)
         crit_c, kern_c = [], []
         for r in range(rounds):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
