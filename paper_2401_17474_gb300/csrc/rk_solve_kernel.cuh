@@ -153,6 +153,32 @@ __device__ __forceinline__ bool bar_and(int id, int nthreads, bool v) {
     return r != 0;
 }
 
+// Sum of the NW warp partials of one slot of `red` (NW a power of two, the slot 16-byte
+// aligned), computed by every thread from vector loads of shared memory in the order of
+// a butterfly over the partials read by lane 0 (pairs at distance NW/2, then NW/4, ...):
+// the same value, bit for bit, in every thread, without shuffles.
+template <int NW>
+__device__ __forceinline__ float cta_sum(const float* slot) {
+    static_assert((NW & (NW - 1)) == 0 && NW <= 32, "warp count");
+    float t[NW];
+    if constexpr (NW >= 4) {
+#pragma unroll
+        for (int i = 0; i < NW / 4; ++i) {
+            const float4 v = reinterpret_cast<const float4*>(slot)[i];
+            t[4 * i] = v.x; t[4 * i + 1] = v.y; t[4 * i + 2] = v.z; t[4 * i + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) t[i] = slot[i];
+    }
+#pragma unroll
+    for (int o = NW / 2; o >= 1; o >>= 1) {
+#pragma unroll
+        for (int l = 0; l < o; ++l) t[l] = t[l] + t[l + o];
+    }
+    return t[0];
+}
+
 __device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity, uint64_t timeout_ns,
                                             int* status) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -709,12 +735,7 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
             float tot[NV];
 #pragma unroll
             for (int u = 0; u < NV; ++u) {
-                float x_ = lane < NW ? red[(rp * kRedSlots + u) * 32 + lane] : 0.f;
-#pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    if (o < NW) x_ += __shfl_xor_sync(0xffffffffu, x_, o);
-                }
-                tot[u] = __shfl_sync(0xffffffffu, x_, 0);
+                tot[u] = cta_sum<NW>(red + (rp * kRedSlots + u) * 32);
             }
             rp ^= 1;
             float c[W];
@@ -806,14 +827,9 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
             for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
             if (lane == 0) red[rp * kRedSlots * 32 + warp] = part;
             if (!bar_and(1, NT, got)) { ok = false; break; }
-            // every warp sums the NW warp partials with the same butterfly, so all
+            // every thread sums the NW warp partials in the same order, so all
             // threads of the CTA hold the same dot
-            float dot = lane < NW ? red[rp * kRedSlots * 32 + lane] : 0.f;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                if (o < NW) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-            }
-            dot = __shfl_sync(0xffffffffu, dot, 0);
+            const float dot = cta_sum<NW>(red + rp * kRedSlots * 32);
             rp ^= 1;
             // A_i = s_i q_i: <A_i, v> = s_i <q_i, v>, d += (scale s_i) q_i
             cprev = p.omega * (mb.x - mb.z * dot) * mb.y * mb.z;
@@ -869,14 +885,9 @@ __global__ void __launch_bounds__(NT + 32, MINB) rkab_kernel(const KParams p) {
             for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
             if (lane == 0) red[rp * kRedSlots * 32 + warp] = part;
             if (!bar_and(1, NT, got)) { ok = false; break; }
-            // every warp sums the NW warp partials with the same butterfly, so all
+            // every thread sums the NW warp partials in the same order, so all
             // threads of the CTA hold the same dot
-            float dot = lane < NW ? red[rp * kRedSlots * 32 + lane] : 0.f;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                if (o < NW) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-            }
-            dot = __shfl_sync(0xffffffffu, dot, 0);
+            const float dot = cta_sum<NW>(red + rp * kRedSlots * 32);
             rp ^= 1;
             // A_i = s_i q_i: <A_i, v> = s_i <q_i, v>, d += (scale s_i) q_i
             const float scale = p.omega * (mb.x - mb.z * dot) * mb.y * mb.z;
