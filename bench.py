@@ -65,7 +65,7 @@ def parse():
                     help="target CPU work of the oracle baseline sample")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-cell, precision and adjoint measurements")
-    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"],
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8", "all"],
                     help="stored rows of the timed solve (bf16/fp8: quantised copy of A)")
     ap.add_argument("--cluster", type=int, default=0,
                     help="CTAs per worker of the timed solve (0/1: one CTA per worker)")
@@ -637,7 +637,8 @@ def _rel64(a, b):
 
 
 def adjoint_c5(rk, dev, seed, sched_fracs=((1.0, 100), (0.1, 300), (0.01, 1500)),
-               rounds_t=24, omega_t=1.0, rounds_g=200, check=True, q_t=6, cluster_t=16, alpha_t=0):
+               rounds_t=3000, omega_t=None, rounds_g=200, check=True, q_t=64, cluster_t=0, alpha_t=1,
+               check_every=50):
     """The differentiation workload at 50000 x 5000 (b = A x* + N(0, 1e-3^2), x_t ~ N(0,1),
     L = 0.5 ||x - x_t||^2) through torch.autograd: the forward RKA solve with 32 workers per
     SM and a decreasing relaxation (alpha* of Eq. (best_alpha), then a tenth, ...: the
@@ -655,11 +656,16 @@ def adjoint_c5(rk, dev, seed, sched_fracs=((1.0, 100), (0.1, 300), (0.01, 1500))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     qa = 32 * sms
     plan = rk.rk_setup(A)
-    w, _ = rk.optimal_weight(A, qa, k=2, plan=plan)
+    w, sp = rk.optimal_weight(A, qa, k=2, plan=plan)
     sched = tuple((w * f, r) for f, r in sched_fracs)
     alpha_t = alpha_t or n
+    if omega_t is None:
+        # RKA on A^T with q_t workers: the rows of A^T have the nonzero singular values of A,
+        # so Eq. (best_alpha) takes A's s_min and s_max with q_t
+        omega_t = rk.alpha_star(q_t, sp.s_min, sp.s_max) if alpha_t == 1 else 1.0
     cfg = rk.AdjointConfig(q=qa, alpha=1, rounds=rounds_g, omega=w, q_t=q_t, cluster_size_t=cluster_t,
-                           alpha_t=alpha_t, rounds_t=rounds_t, omega_t=omega_t, seed=seed + 1)
+                           alpha_t=alpha_t, rounds_t=rounds_t, omega_t=omega_t, seed=seed + 1,
+                           check_every=check_every)
     Ar = A.clone().requires_grad_(True)
     br = b.clone().requires_grad_(True)
     for rep in range(2):   # the first pass warms the autograd engine and the kernels up
@@ -675,8 +681,10 @@ def adjoint_c5(rk, dev, seed, sched_fracs=((1.0, 100), (0.1, 300), (0.01, 1500))
     out = {"workload": f"lstsq_adjoint_{m}x{n}", "forward_ms": round((t1 - t0) * 1e3, 2),
            "backward_ms": round((t2 - t1) * 1e3, 2),
            "forward": f"RKA q={qa}, weights alpha* x " + ", ".join(f"{f:g} ({r} rounds)" for f, r in sched_fracs),
-           "y_solve": f"RKAB on A^T, {q_t} workers of {cluster_t}-CTA clusters, alpha={alpha_t}, {rounds_t} rounds, "
-                      f"omega={omega_t:g}",
+           "y_solve": (f"RKA on A^T with x split by columns over the grid, {q_t} workers, alpha* = {omega_t:.2f}, "
+                       f"{rounds_t} rounds" if alpha_t == 1 and cluster_t <= 1 else
+                       f"RKAB on A^T, {q_t} workers of {cluster_t}-CTA clusters, alpha={alpha_t}, {rounds_t} rounds, "
+                       f"omega={omega_t:g}"),
            "g_solve": f"RKA q={qa}, alpha*, {rounds_g} rounds", "grad_A_bytes": m * n * 4}
     if check:
         xd = x.detach()
@@ -1021,9 +1029,9 @@ def precision_summary(out):
 
 def run_rounds(args, rk, dev):
     """Consumer speed per storage: one RKAB round (q workers, alpha projections each, no
-    checks) on float32, BF16 and FP8 rows of an m x n Gaussian system (defaults 100000 x
-    16000, q = 132, alpha = n), timed --steps times after one untimed launch; --dtype
-    picks one storage (f32: all three)."""
+    checks; 200 rounds a launch for alpha = 1) on float32, BF16 and FP8 rows of an m x n
+    Gaussian system (defaults 100000 x 16000, q = 132, alpha = n), timed --steps times
+    after one untimed launch; --dtype picks one storage (all: the three)."""
     import torch
 
     import rk_inputs
@@ -1034,7 +1042,9 @@ def run_rounds(args, rk, dev):
     plan = rk.rk_setup(A)
     x0 = torch.zeros(n, dtype=torch.float32, device=dev)
     x = torch.empty_like(x0)
-    kinds = ("f32", "bf16", "fp8") if args.dtype == "f32" else (args.dtype,)
+    kinds = ("f32", "bf16", "fp8") if args.dtype == "all" else (args.dtype,)
+    # one round a launch for RKAB; RKA (alpha = 1) rounds are short: 200 a launch
+    rpl = 1 if alpha > 1 else min(args.max_rounds, 200)
     out = {}
     for kind in kinds:
         if kind == "f32":
@@ -1044,20 +1054,20 @@ def run_rounds(args, rk, dev):
             pl, keep = rk.rk_setup(Aq, kind, sc), (Aq, sc)
         s = rk.Solver(pl, q)
         o = rk.make_opts(check_every=0)
-        s.launch(b, x0, x, alpha, 1, 0, o)
+        s.launch(b, x0, x, alpha, rpl, 0, o)
         torch.cuda.synchronize(dev)
         ts = []
         for _ in range(args.steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            s.launch(b, x0, x, alpha, 1, 0, o)
+            s.launch(b, x0, x, alpha, rpl, 0, o)
             e1.record()
             torch.cuda.synchronize(dev)
-            ts.append(e0.elapsed_time(e1))
+            ts.append(e0.elapsed_time(e1) / rpl)
         t = sum(ts) / len(ts)
         eb = {"f32": 4, "bf16": 2, "fp8": 1}[kind]
-        out[kind] = {"ms": round(t, 3), "us_per_row": round(1e3 * t / alpha, 4),
-                     "row_GBps": round(q * alpha * n * eb / (t / 1e3) / 1e9, 1)}
+        out[kind] = {"ms": round(t, 4), "us_per_row": round(1e3 * t / alpha, 4),
+                     "row_GBps": round(q * alpha * n * eb / (t / 1e3) / 1e9, 1), "rounds_a_launch": rpl}
         del s, pl, keep
     return {"workload": f"rkab_round_{m}x{n}_q{q}_alpha{alpha}", "round": out,
             "note": "value unused: this workload times single rounds per storage"}

@@ -210,7 +210,12 @@ size_t rk_solve_workspace_bytes(const rk_plan *plan, int q);
  *   x          device, n floats: result
  *   q          workers: up to twice the SM count (one CTA per worker, two per SM beyond
  *              the SM count; RK_ENOTCORESIDENT beyond), any q >= 1 for alpha = 1 (RKA:
- *              more workers than SMs are spread over one CTA per SM)
+ *              more workers than SMs are spread over one CTA per SM).  Rows too long for
+ *              two shared-memory stages of one CTA (beyond about 27000 float32 columns)
+ *              run RKA only, with 1 <= q <= 64 (x split by columns over one CTA per SM:
+ *              each CTA streams its chunk of every sampled row and the dot products are
+ *              summed across the grid in a fixed order), or RKAB with cluster_size > 1;
+ *              anything else on such rows gives RK_EINVAL
  *   alpha      projections per worker between averages, >= 1
  *   seed       Philox key
  *   opts       NULL for defaults

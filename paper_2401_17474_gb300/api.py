@@ -506,6 +506,7 @@ class AdjointConfig:
     q_t: int = 0              # workers of the solve on A^T (0: q)
     omega_t: float = 1.0      # relaxation of the solve on A^T
     omega: float = 1.0        # relaxation of the solve of A g = y
+    check_every: int = 1      # rounds between the divergence checks of both solves
 
 
 class Adjoint:
@@ -531,10 +532,10 @@ class Adjoint:
         g = torch.empty(n, dtype=torch.float32, device=dev)
         ldg = (n + 3) // 4 * 4
         grad_A = torch.empty((m, ldg), dtype=torch.float32, device=dev)[:, :n]
-        # check_every = 1: no criterion, but a diverging solve ends with RK_EDIVERGED
-        ot = make_opts(omega=c.omega_t, check_every=1, cluster_size=c.cluster_size_t,
+        # no criterion, but a diverging solve ends with RK_EDIVERGED at its next check
+        ot = make_opts(omega=c.omega_t, check_every=c.check_every, cluster_size=c.cluster_size_t,
                        lookahead=c.lookahead)
-        oa = make_opts(omega=c.omega, check_every=1, cluster_size=c.cluster_size,
+        oa = make_opts(omega=c.omega, check_every=c.check_every, cluster_size=c.cluster_size,
                        lookahead=c.lookahead)
         check(_lib.load().rkab_adjoint(self.plan_A.handle, self.plan_At.handle, _ptr(b), _ptr(x),
                                        _ptr(gx), c.q_t or c.q, c.q, c.alpha_t or n, c.rounds_t,

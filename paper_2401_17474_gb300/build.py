@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["rk_api.cu", "rk_setup.cu", "rk_solve.cu", "rk_solve_f32.cu", "rk_solve_bf16.cu",
            "rk_solve_fp8.cu", "rk_cluster_f32.cu", "rk_cluster_bf16.cu", "rk_cluster_fp8.cu",
            "rk_residual.cu", "rk_precision.cu", "rk_adjoint.cu", "rk_noalloc.cu",
-           "rk_spectrum.cu"]
+           "rk_spectrum.cu", "rk_colsplit.cu"]
 
 
 def nvcc() -> str:

@@ -1,0 +1,530 @@
+// rk_colsplit.cu -- RKA (alpha = 1; Algorithm 1, Eq. (rka_uni_weights), Eq. (rka_eq))
+// with the columns of x split across the grid, for rows too long for one CTA's
+// shared memory (the rows of A^T in the adjoint's minimum-norm solve, 200 KB to
+// 800 KB): every one of the G CTAs (one per SM) owns a contiguous chunk of x's
+// columns and, each round, streams that chunk of all q sampled rows.
+//
+// Round k, in every CTA g:
+//   1. partial dots p_j^g = <A_j[chunk g], x[chunk g]> of the q rows j (the
+//      round's draws of workers 0 .. q-1, the same draws as the one-CTA kernels:
+//      worker j's projection counter is the round index), formed eight rows to a
+//      pass and reduced across the CTA's warps;
+//   2. the q partials go to global memory (double-buffered by round parity), one
+//      grid barrier;
+//   3. every CTA sums the G partials of each row in the same fixed order,
+//      <A_j, x> = sum_g p_j^g, and forms c_j = omega w_j (b_j - <A_j, x>) / ||A_j||^2;
+//   4. d = sum_j c_j A_j[chunk g] (ascending j), x[chunk g] += d / q: the average of
+//      the q projections of Eq. (rka_uni_weights), held in the difference form.
+// The stages of a round are released after step 4, so the ring holds at least the
+// round's q rows; the producer fills the rest with the next round's rows. Checks
+// (criterion, divergence) add a second grid barrier on the rounds they run.
+#include "rk_solve_kernel.cuh"
+
+namespace rk {
+
+constexpr int kCsMaxQ = 64;    // workers a round (colsplit_fits in rk_internal.h)
+constexpr int kCsGroup = 8;    // rows whose partial dots one pass forms
+constexpr int kCsProd = 4;     // producer warps (the ring's stage count is a multiple)
+
+struct CSParams {
+    KParams k;
+    int chunk;          // slices (4 elements) of x per CTA, a multiple of 4
+    float* part;        // [2][G][kCsMaxQ] partial dots (round parity, CTA, worker)
+};
+
+// Shared memory after the stages: full[S] + empty[S] mbarriers, meta[S] float4,
+// red[kCsMaxQ][NW] warp partials, grp[NT / 16][16] float4 partial sums of the grid
+// reduction, cvec[kCsMaxQ] coefficients, chk[96] double, pbuf[32] float4, Ctrl.
+__host__ __device__ inline size_t cs_ctrl_bytes(int S, int nt) {
+    const int nw = nt / 32;
+    return (size_t)S * 16 + (size_t)S * 16 + (size_t)kCsMaxQ * nw * 4 + (size_t)nt * 16 + kCsMaxQ * 4 +
+           96 * 8 + kCsProd * 32 * 16 + 64;
+}
+
+// Bytes of this CTA's chunk of a row: nl slices of 4 elements, rounded up to 16 bytes
+// (which stays inside the row's lda extent: chunks start at multiples of 4 slices).
+template <int ELT>
+__device__ __forceinline__ uint32_t cs_copy_bytes(int nl) {
+    constexpr uint32_t eb = ELT == ELT_F32 ? 4u : (ELT == ELT_BF16 ? 2u : 1u);
+    return ((uint32_t)nl * 4u * eb + 15u) & ~15u;
+}
+
+// 16-byte asynchronous copy global -> shared (the L1-bypassing form), and the arrive on
+// an mbarrier that fires once this thread's earlier asynchronous copies have landed (the
+// barrier's expected count includes it: .noinc).
+__device__ __forceinline__ void cs_cp16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cs_cp_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Producer warps: rows of the q workers, round after round, into the ring (this
+// CTA's chunk of each row).  Sequence index u = round * q + j uses stage u mod S.
+// kCsProd warps share the rows: warp pw takes u = pw, pw + kCsProd, ... in order; S is
+// a multiple of kCsProd, so a stage is always filled by the same warp and its empty
+// barrier is at most one phase behind that warp's next use (the parity wait stays
+// unambiguous).  A warp draws 32 of its rows at once; then, row after row, the whole
+// warp copies the row's chunk in 16-byte pieces (consecutive lanes, consecutive pieces:
+// one 512-byte coalesced request an instruction) and every lane arrives on the stage's
+// full barrier when its pieces land; lane 0 also arrives after writing the row's b_i,
+// 1/||A_i||^2 and scale (the barrier expects 33 arrivals a phase).
+template <int ELT>
+__device__ void cs_producer(const CSParams& cp, uint8_t* stages, uint64_t* full, uint64_t* empty,
+                            float4* meta, volatile Ctrl* ctrl, float4* pbuf, int c0, int pw) {
+    const KParams& p = cp.k;
+    const int lane = threadIdx.x & 31;
+    const int S = p.stages;
+    const int q = p.q;
+    const int64_t total = p.rounds * (int64_t)q;
+    const int64_t mine = total > pw ? (total - pw + kCsProd - 1) / kCsProd : 0;   // rows of this warp
+    constexpr uint32_t eb = ELT == ELT_F32 ? 4u : (ELT == ELT_BF16 ? 2u : 1u);
+    const uint8_t* Ac = p.A + (size_t)c0 * 4u * eb;
+    const int nl = max(0, min(p.n4 - c0, cp.chunk));
+    const int pieces = (int)(cs_copy_bytes<ELT>(nl) / 16u);
+    int* status = &p.info->status;
+    int s = pw;               // stage of this warp's next row (S is a multiple of kCsProd)
+    uint32_t pass = 0;
+    bool stop = false;
+    for (int64_t base = 0; base < mine && !stop; base += 32) {
+        const int64_t il = base + lane;
+        if (il < mine) {
+            const int64_t tl = il * kCsProd + pw;                    // sequence index
+            const uint32_t own = (uint32_t)(tl % q);                 // worker j
+            const uint64_t tt = (uint64_t)p.round0 + (uint64_t)(tl / q);
+            uint32_t row = draw_row(p, p.same_stream ? 0u : own, tt);
+            if (row >= p.m) {   // a row block of zero weight: nothing to draw
+                set_status(status, RK_EINVAL);
+                row = 0;
+            }
+            const float sc = (ELT == ELT_FP8) ? __ldg(p.row_scale + row) : 1.f;
+            float wi = p.row_weight ? __ldg(p.row_weight + row) : 1.f;
+            if (p.worker_weight) wi *= __ldg(p.worker_weight + own);
+            pbuf[lane] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row) * wi, sc);
+        }
+        __syncwarp();
+        const int64_t rem_ = mine - base;
+        const int cnt = rem_ < 32 ? (int)rem_ : 32;
+        for (int k = 0; k < cnt; ++k) {
+            const int64_t tt = (base + k) * kCsProd + pw;
+            bool go = tt < ctrl->stop_t;
+            if (go && tt >= S && lane == 0) {
+                // the previous copy into this stage (the last pass's) was consumed
+                const uint32_t prev = pass ^ 1u;
+                if (!mbar_try_wait(&empty[s], prev)) {
+                    const uint64_t t0 = globaltimer_ns();
+                    while (!mbar_try_wait(&empty[s], prev)) {
+                        if (tt >= ctrl->stop_t) { go = false; break; }
+                        if (globaltimer_ns() - t0 > p.timeout_ns) {
+                            set_status(status, RK_ETIMEOUT);
+                            go = false;
+                            break;
+                        }
+                    }
+                }
+            }
+            go = __shfl_sync(0xffffffffu, go, 0);
+            if (!go) { stop = true; break; }
+            const float4 e = pbuf[k];
+            const uint8_t* src = Ac + (size_t)__float_as_uint(e.x) * (size_t)p.lda_bytes;
+            uint8_t* dst = stages + (size_t)s * p.stage_stride;
+            for (int pc = lane; pc < pieces; pc += 32) cs_cp16(dst + (size_t)pc * 16, src + (size_t)pc * 16);
+            cs_cp_arrive(&full[s]);
+            if (lane == 0) {
+                meta[s] = make_float4(e.y, e.z, e.w, 0.f);
+                mbar_arrive(&full[s]);
+            }
+            s += kCsProd;
+            if (s >= S) { s -= S; pass ^= 1u; }
+        }
+        __syncwarp();
+    }
+    // every copy this warp issued must land before the CTA exits
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+}
+
+// Slice idx (0 .. NT*VPT-1) of this CTA's chunk of a staged row, widened to float32:
+// zero beyond the CTA's nl slices (not read: the stage holds only the chunk), and the
+// row's last slice masked past column n.
+template <int ELT>
+__device__ __forceinline__ float4 cs_slice(const uint8_t* stg, int idx, int nl, bool is_tail, int rem) {
+    if (idx >= nl) return make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 a = load4<ELT>(stg, idx);
+    if (is_tail) a = zero_beyond(a, rem);
+    return a;
+}
+
+template <int NT, int VPT, int ELT>
+__global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(const CSParams cp) {
+    const KParams& p = cp.k;
+    extern __shared__ __align__(128) uint8_t smem[];
+    constexpr int NW = NT / 32;
+    const int S = p.stages;
+    const int q = p.q;
+    uint8_t* stages = smem;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * p.stage_stride);
+    uint64_t* empty = full + S;
+    float4* meta = reinterpret_cast<float4*>(empty + S);
+    float* red = reinterpret_cast<float*>(meta + S);           // [kCsMaxQ][NW]
+    float4* grp = reinterpret_cast<float4*>(red + kCsMaxQ * NW);   // [NT / 16][16]
+    float* cvec = reinterpret_cast<float*>(grp + NT);            // [kCsMaxQ]
+    double* chk = reinterpret_cast<double*>(cvec + kCsMaxQ);    // [96]
+    float4* pbuf = reinterpret_cast<float4*>(chk + 96);         // [kCsProd][32] the producers' draws
+    volatile Ctrl* ctrl = reinterpret_cast<volatile Ctrl*>(pbuf + 32 * kCsProd);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int G = (int)gridDim.x;
+    const int g = (int)blockIdx.x;
+    const int c0 = g * cp.chunk;                          // first slice of x this CTA owns
+    const int nl = max(0, min(p.n4 - c0, cp.chunk));      // slices it owns
+    const int64_t total = p.rounds * (int64_t)q;
+    int* status = &p.info->status;
+
+    {
+        uint4* z = reinterpret_cast<uint4*>(stages);
+        const size_t nz = (size_t)S * p.stage_stride / 16;
+        for (size_t i = tid; i < nz; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 33);   // 32 copying lanes + lane 0's row data
+            mbar_init(&empty[i], NW);
+        }
+        ctrl->stop_t = total;
+        ctrl->flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (p.setup->status != 0) {
+        if (tid == 0) set_status(status, RK_ESETUP);
+        return;
+    }
+    if (p.sampling == RK_SAMPLE_CYCLIC && p.setup->range_rows != 0) {
+        if (tid == 0) set_status(status, RK_EINVAL);
+        return;
+    }
+    if (warp >= NW) {
+        const int pw = warp - NW;
+        cs_producer<ELT>(cp, stages, full, empty, meta, ctrl, pbuf + 32 * pw, c0, pw);
+        return;
+    }
+
+    // ---------------- consumers ----------------
+    const int rem = p.n & 3;
+    int tail_k = -1;   // k of the row's last slice for the thread that owns it (rem != 0)
+    {
+        const int lt = p.n4 - 1 - c0;   // local index of the last slice
+        if (rem && lt >= 0 && lt < nl && (lt % NT) == tid) tail_k = lt / NT;
+    }
+    float4 v[VPT];   // this CTA's chunk of x (the round's start point)
+    float4 d[VPT];   // the round's sum of c_j A_j over the chunk
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+        const int idx = tid + k * NT;
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < nl) {
+            const int j = (c0 + idx) * 4;
+            t.x = __ldg(p.x0 + j);
+            if (j + 1 < p.n) t.y = __ldg(p.x0 + j + 1);
+            if (j + 2 < p.n) t.z = __ldg(p.x0 + j + 2);
+            if (j + 3 < p.n) t.w = __ldg(p.x0 + j + 3);
+        }
+        v[k] = t;
+        d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float rq = 1.0f / (float)q;
+    int64_t u = 0;                 // sequence index of the round's first row
+    int s0 = 0;                    // its stage (u mod S) ...
+    uint32_t ph0 = 0;              // ... and the parity of its pass over the ring
+    // stage and parity of the round's row j (j < q <= S: at most one wrap)
+    auto stage_of = [&](int j, uint32_t& par) {
+        int st = s0 + j;
+        par = ph0;
+        if (st >= S) { st -= S; par ^= 1u; }
+        return st;
+    };
+    unsigned long long nbar = 0;   // grid barriers passed
+    bool ok = true;
+    for (int64_t r = 0; r < p.rounds && ok; ++r) {
+        const int rb = (int)(r & 1);
+        // ---- 1. partial dots of the chunk, kCsGroup rows a pass ----
+        bool got = true;
+        for (int j0 = 0; j0 < q; j0 += kCsGroup) {
+            const int cnt = min(kCsGroup, q - j0);
+            float acc[kCsGroup];
+            int sg[kCsGroup];
+#pragma unroll
+            for (int rr = 0; rr < kCsGroup; ++rr) {
+                acc[rr] = 0.f;
+                sg[rr] = 0;
+                if (rr < cnt) {
+                    uint32_t par;
+                    sg[rr] = stage_of(j0 + rr, par);
+                    got = wait_parity(&full[sg[rr]], par, p.timeout_ns, status) && got;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int idx = tid + k * NT;
+                const float4 xk = v[k];
+#pragma unroll
+                for (int rr = 0; rr < kCsGroup; ++rr) {
+                    if (rr < cnt) {
+                        const float4 a = cs_slice<ELT>(stages + (size_t)sg[rr] * p.stage_stride, idx, nl,
+                                                       k == tail_k, rem);
+                        float t = acc[rr];
+                        t = fmaf(a.x, xk.x, t);
+                        t = fmaf(a.y, xk.y, t);
+                        t = fmaf(a.z, xk.z, t);
+                        t = fmaf(a.w, xk.w, t);
+                        acc[rr] = t;
+                    }
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < kCsGroup; ++rr) {
+#pragma unroll
+                for (int o = 16; o; o >>= 1) acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], o);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int rr = 0; rr < kCsGroup; ++rr)
+                    if (rr < cnt) red[(j0 + rr) * NW + warp] = acc[rr];
+            }
+        }
+        if (!bar_and(1, NT, got)) { ok = false; break; }
+        // ---- 2. this CTA's partials to global memory, one grid barrier ----
+        if (warp == 0) {
+            float* pg = cp.part + ((size_t)rb * G + g) * kCsMaxQ;
+            for (int j = lane; j < q; j += 32) pg[j] = cta_sum<NW>(red + j * NW);
+            named_bar_sync(2, 32);
+            if (lane == 0)
+                ctrl->flag = grid_sync(&p.info->bar_arrivals, nbar, (unsigned)G, status, p.timeout_ns) ? 1 : 0;
+        }
+        ++nbar;
+        named_bar_sync(1, NT);
+        if (!ctrl->flag) { ok = false; break; }
+        // ---- 3. <A_j, x> = sum_g p_j^g in a fixed order, the coefficients ----
+        // thread (h, f) sums float4 f (workers 4f .. 4f+3) of the CTAs g = h, h + H, ...
+        // in ascending g, all its loads in flight at once; then each worker's total is
+        // the sum over h in ascending order: the same order in every CTA
+        {
+            constexpr int H = NT / 16;
+            constexpr int B = 16;   // loads in flight a thread (152 CTAs / 16 groups)
+            const int f = tid & 15, h = tid >> 4;
+            const float4* pr4 = reinterpret_cast<const float4*>(cp.part + (size_t)rb * G * kCsMaxQ);
+            float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (4 * f < q) {
+                for (int g0 = h; g0 < G; g0 += H * B) {
+                    float4 w[B];
+#pragma unroll
+                    for (int e = 0; e < B; ++e) {
+                        const int gg = g0 + e * H;
+                        w[e] = gg < G ? __ldcg(pr4 + (size_t)gg * (kCsMaxQ / 4) + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int e = 0; e < B; ++e) {
+                        t4.x += w[e].x; t4.y += w[e].y; t4.z += w[e].z; t4.w += w[e].w;
+                    }
+                }
+            }
+            grp[h * 16 + f] = t4;
+        }
+        named_bar_sync(1, NT);
+        for (int j = tid; j < q; j += NT) {
+            const float* gj = reinterpret_cast<const float*>(grp) + j;   // component j % 4 of float4 j / 4
+            float dot = 0.f;
+            for (int h = 0; h < NT / 16; ++h) dot += gj[h * 64];
+            uint32_t par;
+            const float4 mb = meta[stage_of(j, par)];   // b_j, w_j / ||A_j||^2, row scale s_j
+            // A_j = s_j q_j: <A_j, x> = s_j <q_j, x>, and the update takes (c_j s_j) q_j
+            cvec[j] = p.omega * (mb.x - mb.z * dot) * mb.y * mb.z;
+        }
+        named_bar_sync(1, NT);
+        // ---- 4. d = sum_j c_j A_j[chunk] in ascending j, then x += d / q ----
+        // UJ rows a step, their coefficients and slices loaded together
+        constexpr int UJ = VPT <= 2 ? 4 : (VPT <= 4 ? 2 : 1);
+        for (int j0 = 0; j0 < q; j0 += UJ) {
+            float c[UJ];
+            float4 a[UJ][VPT];
+#pragma unroll
+            for (int jj = 0; jj < UJ; ++jj) {
+                const int j = j0 + jj;
+                c[jj] = j < q ? cvec[j] : 0.f;
+                uint32_t par;
+                const uint8_t* stg = stages + (size_t)stage_of(j < q ? j : j0, par) * p.stage_stride;
+#pragma unroll
+                for (int k = 0; k < VPT; ++k)
+                    a[jj][k] = j < q ? cs_slice<ELT>(stg, tid + k * NT, nl, k == tail_k, rem)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int jj = 0; jj < UJ; ++jj) {
+                const float2 c2 = make_float2(c[jj], c[jj]);
+#pragma unroll
+                for (int k = 0; k < VPT; ++k) {
+                    const float2 lo = __ffma2_rn(c2, make_float2(a[jj][k].x, a[jj][k].y), make_float2(d[k].x, d[k].y));
+                    const float2 hi = __ffma2_rn(c2, make_float2(a[jj][k].z, a[jj][k].w), make_float2(d[k].z, d[k].w));
+                    d[k] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                }
+            }
+        }
+        __syncwarp();
+        // this warp's release of the round's stages, one lane a stage
+        for (int j = lane; j < q; j += 32) {
+            uint32_t par;
+            mbar_arrive(&empty[stage_of(j, par)]);
+        }
+        u += q;
+        s0 += q;
+        if (s0 >= S) { s0 -= S; ph0 ^= 1u; }
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            v[k] = make_float4(fmaf(d[k].x, rq, v[k].x), fmaf(d[k].y, rq, v[k].y), fmaf(d[k].z, rq, v[k].z),
+                               fmaf(d[k].w, rq, v[k].w));
+            d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // ---- 5. convergence / divergence check (a second grid barrier) ----
+        const int64_t done = r + 1;
+        const bool last = (done == p.rounds);
+        const bool check = p.check_every > 0 && (done % p.check_every == 0 || last);
+        if (check) {
+            ChkAcc ca{0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int idx = tid + k * NT;
+                if (idx < nl) {
+                    const int j = (c0 + idx) * 4;
+                    const float vv[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (j + e < p.n) {
+                            ca.xx = fmaf(vv[e], vv[e], ca.xx);
+                            if (p.criterion == 1) {
+                                const float xr = __ldg(p.x_ref + j + e);
+                                const float dd = vv[e] - xr;
+                                ca.e2 = fmaf(dd, dd, ca.e2);
+                                ca.r2 = fmaf(xr, xr, ca.r2);
+                            }
+                        }
+                    }
+                }
+            }
+            check_warp_partials<NT>(ca, chk);
+            named_bar_sync(1, NT);
+            if (tid == 0) {
+                check_cta_partial<NT>(p, chk);
+                ctrl->flag = grid_sync(&p.info->bar_arrivals, nbar, (unsigned)G, status, p.timeout_ns) ? 1 : 0;
+            }
+            ++nbar;
+            named_bar_sync(1, NT);
+            if (!ctrl->flag) { ok = false; break; }
+            combine_check<NT>(p, chk);
+            const float* sh = reinterpret_cast<const float*>(chk);
+            const float XX = sh[0], E2 = sh[1], R2 = sh[2];
+            named_bar_sync(1, NT);
+            float mf = -1.f;
+            if (p.criterion == 1) mf = (R2 > 0.f) ? sqrtf(E2 / R2) : sqrtf(E2);
+            const double metric = (double)mf;
+            const bool diverged = !isfinite(XX) || (p.criterion == 1 && !isfinite(mf));
+            if (g == 0 && tid == 0) {
+                p.info->rounds_done = done;
+                p.info->last_metric = metric;
+            }
+            if (diverged) {
+                if (tid == 0) set_status(status, RK_EDIVERGED);
+                ok = false;
+            } else if (p.criterion == 1 && p.tol > 0.0 && metric < p.tol) {
+                break;   // converged: the same decision in every CTA
+            }
+        } else if (g == 0 && tid == 0) {
+            p.info->rounds_done = done;
+        }
+    }
+    // stop the producer at what was consumed, and write this CTA's chunk of x
+    if (tid == 0) ctrl->stop_t = u;
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+        const int idx = tid + k * NT;
+        if (idx < nl) {
+            const int j = (c0 + idx) * 4;
+            p.x[j] = v[k].x;
+            if (j + 1 < p.n) p.x[j + 1] = v[k].y;
+            if (j + 2 < p.n) p.x[j + 2] = v[k].z;
+            if (j + 3 < p.n) p.x[j + 3] = v[k].w;
+        }
+    }
+}
+
+typedef void (*CsKernelFn)(const CSParams);
+
+struct CsVariant {
+    int nt, vpt, elt;
+    CsKernelFn fn;
+};
+
+// 256 consumer threads whatever the chunk: the grid reduction of each round wants
+// many loads in flight, and idle threads cost nothing in the other phases
+#define CS_(NT, VPT, ELT) CsVariant{NT, VPT, ELT, rka_colsplit_kernel<NT, VPT, ELT>}
+static const CsVariant kCsTab[] = {
+    CS_(256, 1, ELT_F32),  CS_(256, 2, ELT_F32),  CS_(256, 4, ELT_F32),  CS_(256, 8, ELT_F32),
+    CS_(256, 1, ELT_BF16), CS_(256, 2, ELT_BF16), CS_(256, 4, ELT_BF16), CS_(256, 8, ELT_BF16),
+    CS_(256, 1, ELT_FP8),  CS_(256, 2, ELT_FP8),  CS_(256, 4, ELT_FP8),  CS_(256, 8, ELT_FP8),
+};
+#undef CS_
+
+int launch_colsplit_solve(const SolveArgs& a, const KParams& base, cudaStream_t st, int smem_max, int sms) {
+    const Plan* pl = a.plan;
+    if (a.q < 1 || a.q > kCsMaxQ) return RK_EINVAL;
+    const int n4 = base.n4;
+    const int chunk = ((n4 + sms - 1) / sms + 3) / 4 * 4;
+    const int grid = (n4 + chunk - 1) / chunk;
+    const int nt = 256;
+    const int elt = pl->dt == RK_F32 ? ELT_F32 : (pl->dt == RK_BF16 ? ELT_BF16 : ELT_FP8);
+    const CsVariant* var = nullptr;   // the fewest slices a thread that cover the chunk
+    for (const CsVariant& v : kCsTab)
+        if (v.nt == nt && v.elt == elt && v.vpt * nt >= chunk && (!var || v.vpt < var->vpt)) var = &v;
+    if (!var) return RK_EINVAL;   // rows beyond 8192 x 4 x SMs columns
+    const uint32_t eb = pl->dt == RK_F32 ? 4u : (pl->dt == RK_BF16 ? 2u : 1u);
+    // a stage holds one chunk (the kernel reads no slice past the CTA's own)
+    const uint32_t stride = ((uint32_t)chunk * 4u * eb + 127u) & ~127u;
+    // every stage of a round stays taken until its update: at least q stages; up to
+    // twice that lets the producer fetch the next round during the exchange
+    int S = 0;
+    while (S < 2 * a.q + kCsGroup && S < 252 &&
+           (size_t)(S + 1) * stride + cs_ctrl_bytes(S + 1, nt) <= (size_t)smem_max)
+        ++S;
+    S -= S % kCsProd;   // each producer warp serves its own stages
+    if (S < a.q) return RK_EINVAL;   // the round's rows do not fit the shared memory
+    // partial dots (2 x grid x kCsMaxQ floats) and the per-CTA check partials (grid
+    // float4) in the V block of the solve workspace: (v_rows + 1) x ldv floats
+    const size_t part_floats = (size_t)2 * grid * kCsMaxQ;
+    const size_t have = (size_t)(v_rows_for(a.q, a.alpha) + 1) * (size_t)a.ldv;
+    if (part_floats + (size_t)grid * 4 + 4 > have) return RK_EINVAL;
+    CSParams cp;
+    cp.k = base;
+    cp.k.stages = S;
+    cp.k.stage_stride = stride;
+    cp.k.row_bytes = 0;   // per-CTA copy sizes are computed in the kernel
+    cp.k.chkpart = a.V + ((part_floats + 3) & ~(size_t)3);
+    cp.chunk = chunk;
+    cp.part = a.V;
+    const size_t smem = (size_t)S * stride + cs_ctrl_bytes(S, nt);
+    if (cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return RK_ECUDA;
+    void* args[] = {(void*)&cp};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)var->fn, dim3((unsigned)grid),
+                                                dim3((unsigned)(nt + 32 * kCsProd)), args, smem, st);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+        cudaGetLastError();
+        return RK_ENOTCORESIDENT;
+    }
+    if (e != cudaSuccess) return RK_ECUDA;
+    count_launch();
+    return RK_OK;
+}
+
+}  // namespace rk

@@ -98,6 +98,9 @@ size_t solve_ws_bytes_for(const Plan* plan, int q, int64_t alpha);     // what (
 bool sampling_ok(const rk_opts& o);
 bool solve_opts_valid(const rk_opts& o, int q);                        // the solves' option checks
 int launch_solve(const SolveArgs& a, cudaStream_t st);
+// RKA (alpha = 1) on rows too long for one CTA: x split by columns over the grid,
+// up to 64 workers a round
+inline bool colsplit_fits(int64_t alpha, int q) { return alpha == 1 && q >= 1 && q <= 64; }
 int launch_sample_indices(const Plan* plan, uint64_t seed, uint32_t worker, uint32_t stream_id,
                           uint64_t t0, int64_t count, uint32_t* out, cudaStream_t st);
 

@@ -84,6 +84,8 @@ static int stages_for(uint32_t stride, int nt, int smem_max) {
     return S;
 }
 
+int launch_colsplit_solve(const SolveArgs& a, const KParams& base, cudaStream_t st, int smem_max, int sms);
+
 // Cluster path: each worker is a cluster of C CTAs splitting the row's columns.
 static int launch_cluster_solve(const SolveArgs& a, const KParams& base, int C, cudaStream_t st,
                                 int smem_max) {
@@ -264,7 +266,7 @@ int launch_solve(const SolveArgs& a, cudaStream_t st) {
     int S = 0;
     for (int attempt = 0; attempt < 3; ++attempt) {
         const SolveVariant* v1 = pick_variant(pl->dt, n4, 1, 1, jac);
-        if (!v1) return RK_EINVAL;
+        if (!v1) break;   // no one-CTA variant holds the row
         // measured: groups of 4 pay off only with a single consumer warp (n <= 512);
         // from 128 consumers up, one row at a time is faster (0.34 against 0.40 us a
         // row at n = 1000, 0.43 against 0.63-0.66 at n = 4000)
@@ -279,7 +281,12 @@ int launch_solve(const SolveArgs& a, cudaStream_t st) {
         w = var->w > 1 ? var->w / 2 : 1;   // fewer rows per group when the ring is short
         var = nullptr;
     }
-    if (!var || S < 2) return RK_EINVAL;
+    if (!var || S < 2) {
+        // a row too long for two stages of one CTA: RKA runs with x split by columns
+        // over the grid (rk_colsplit.cu), every CTA streaming its chunk of each row
+        if (colsplit_fits(a.alpha, a.q)) return launch_colsplit_solve(a, base_params(a), st, smem_max, sms);
+        return RK_EINVAL;
+    }
     const size_t smem = (size_t)S * stride + xs_bytes(var) + solve_ctrl_bytes(S, var->nt);
 
     KParams p = base_params(a);
