@@ -7,14 +7,16 @@
 // Round k, in every CTA g:
 //   1. partial dots p_j^g = <A_j[chunk g], x[chunk g]> of the q rows j (the
 //      round's draws of workers 0 .. q-1, the same draws as the one-CTA kernels:
-//      worker j's projection counter is the round index), formed eight rows to a
-//      pass and reduced across the CTA's warps;
+//      worker j's projection counter is the round index), warp w forming rows
+//      w, w + 8, ... whole over the chunk (x's chunk is held in shared memory);
 //   2. the q partials go to global memory (double-buffered by round parity), one
 //      grid barrier;
 //   3. every CTA sums the G partials of each row in the same fixed order,
 //      <A_j, x> = sum_g p_j^g, and forms c_j = omega w_j (b_j - <A_j, x>) / ||A_j||^2;
-//   4. d = sum_j c_j A_j[chunk g] (ascending j), x[chunk g] += d / q: the average of
-//      the q projections of Eq. (rka_uni_weights), held in the difference form.
+//   4. d = sum_j c_j A_j[chunk g], x[chunk g] += d / q: the average of the q
+//      projections of Eq. (rka_uni_weights), held in the difference form (the rows
+//      split into P groups so that every thread has slices to sum; the group sums
+//      added in a fixed order).
 // The stages of a round are released after step 4, so the ring holds at least the
 // round's q rows; the producer fills the rest with the next round's rows. Checks
 // (criterion, divergence) add a second grid barrier on the rounds they run.
@@ -23,21 +25,24 @@
 namespace rk {
 
 constexpr int kCsMaxQ = 64;    // workers a round (colsplit_fits in rk_internal.h)
-constexpr int kCsGroup = 8;    // rows whose partial dots one pass forms
+constexpr int kCsSpare = 8;    // ring stages beyond two rounds' rows
 constexpr int kCsProd = 4;     // producer warps (the ring's stage count is a multiple)
 
 struct CSParams {
     KParams k;
     int chunk;          // slices (4 elements) of x per CTA, a multiple of 4
+    int groups;         // P: row groups of the update (P x chunk <= consumer threads, or 1)
     float* part;        // [2][G][kCsMaxQ] partial dots (round parity, CTA, worker)
 };
 
 // Shared memory after the stages: full[S] + empty[S] mbarriers, meta[S] float4,
-// red[kCsMaxQ][NW] warp partials, grp[NT / 16][16] float4 partial sums of the grid
-// reduction, cvec[kCsMaxQ] coefficients, chk[96] double, pbuf[32] float4, Ctrl.
-__host__ __device__ inline size_t cs_ctrl_bytes(int S, int nt) {
-    const int nw = nt / 32;
-    return (size_t)S * 16 + (size_t)S * 16 + (size_t)kCsMaxQ * nw * 4 + (size_t)nt * 16 + kCsMaxQ * 4 +
+// xs[XP] float4 (this CTA's chunk of x, XP = chunk rounded up to 32 slices),
+// dpart[P][chunk] float4 (the update's group sums, P > 1 only), grp[NT / 16][16]
+// float4 (partial sums of the grid reduction), rowc[kCsMaxQ] float2 (c_j and row j's
+// stage offset), chk[96] double, pbuf[kCsProd][32] float4, Ctrl.
+__host__ __device__ inline size_t cs_ctrl_bytes(int S, int nt, int chunk, int P) {
+    const size_t xp = (size_t)(chunk + 31) / 32 * 32;
+    return (size_t)S * 32 + xp * 16 + (P > 1 ? (size_t)P * chunk * 16 : 0) + (size_t)nt * 16 + kCsMaxQ * 8 +
            96 * 8 + kCsProd * 32 * 16 + 64;
 }
 
@@ -114,6 +119,9 @@ __device__ void cs_producer(const CSParams& cp, uint8_t* stages, uint64_t* full,
                 if (!mbar_try_wait(&empty[s], prev)) {
                     const uint64_t t0 = globaltimer_ns();
                     while (!mbar_try_wait(&empty[s], prev)) {
+                        // the ring is a round ahead: back off, leaving the issue slots and
+                        // the shared-memory pipe to the consumers
+                        __nanosleep(256);
                         if (tt >= ctrl->stop_t) { go = false; break; }
                         if (globaltimer_ns() - t0 > p.timeout_ns) {
                             set_status(status, RK_ETIMEOUT);
@@ -144,33 +152,110 @@ __device__ void cs_producer(const CSParams& cp, uint8_t* stages, uint64_t* full,
     __syncwarp();
 }
 
-// Slice idx (0 .. NT*VPT-1) of this CTA's chunk of a staged row, widened to float32:
-// zero beyond the CTA's nl slices (not read: the stage holds only the chunk), and the
-// row's last slice masked past column n.
-template <int ELT>
-__device__ __forceinline__ float4 cs_slice(const uint8_t* stg, int idx, int nl, bool is_tail, int rem) {
-    if (idx >= nl) return make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 a = load4<ELT>(stg, idx);
-    if (is_tail) a = zero_beyond(a, rem);
-    return a;
+// wait_parity with a short back-off between polls (the waits of this kernel are for
+// rows a round ahead of the copies; tight polling only steals issue slots)
+__device__ __forceinline__ bool cs_wait(uint64_t* bar, uint32_t parity, uint64_t timeout_ns, int* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        __nanosleep(64);
+        if (globaltimer_ns() - t0 > timeout_ns) {
+            set_status(status, RK_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
 }
 
-template <int NT, int VPT, int ELT>
+// The partial dots of R (<= 8) staged rows against this CTA's chunk of x, the lanes of
+// the warp taking consecutive slices (lane + 32 i): each lane's sums over its slices,
+// acc[rr] for row rr.  Slices past the chunk read nothing; the row's last slice is
+// masked past column n (its elements there are the row's padding).
+template <int ELT, int R>
+__device__ __forceinline__ void cs_dot_rows(const uint8_t* stages, const uint32_t* off, const float4* xs, int nl,
+                                            bool has_tail, int rem, float* acc) {
+    const int lane = threadIdx.x & 31;
+    const int L = (nl + 31) >> 5;
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) acc[rr] = 0.f;
+    for (int i = 0; i + 1 < L; ++i) {
+        const int idx = lane + 32 * i;
+        const float4 xk = xs[idx];
+        float4 a[R];
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) a[rr] = load4<ELT>(stages + off[rr], idx);
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr)
+            acc[rr] = fmaf(a[rr].w, xk.w, fmaf(a[rr].z, xk.z, fmaf(a[rr].y, xk.y, fmaf(a[rr].x, xk.x, acc[rr]))));
+    }
+    const int idx = lane + 32 * (L - 1);
+    if (L > 0 && idx < nl) {
+        const float4 xk = xs[idx];
+        const bool tail = has_tail && idx == nl - 1;
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+            float4 a = load4<ELT>(stages + off[rr], idx);
+            if (tail) a = zero_beyond(a, rem);
+            acc[rr] = fmaf(a.w, xk.w, fmaf(a.z, xk.z, fmaf(a.y, xk.y, fmaf(a.x, xk.x, acc[rr]))));
+        }
+    }
+}
+
+// Sums over the warp of eight per-lane values at once (a transposed butterfly: at
+// each of the first three steps a lane keeps half of its values and sends the other
+// half to its partner, 4 + 2 + 1 shuffles, then two plain steps).  Returns, in every
+// lane l, the warp's total of value 4 b4 + 2 b3 + b2 (bk = bit k of l).  The order of
+// the additions is fixed, so the result is the same on every run.
+__device__ __forceinline__ float cs_reduce8(const float* acc) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = b4 ? acc[k] : acc[k + 4];
+        const float keep = b4 ? acc[k + 4] : acc[k];
+        h[k] = keep + __shfl_xor_sync(FULL, send, 16);
+    }
+    float t[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = b3 ? h[k] : h[k + 2];
+        const float keep = b3 ? h[k + 2] : h[k];
+        t[k] = keep + __shfl_xor_sync(FULL, send, 8);
+    }
+    float u;
+    {
+        const float send = b2 ? t[0] : t[1];
+        const float keep = b2 ? t[1] : t[0];
+        u = keep + __shfl_xor_sync(FULL, send, 4);
+    }
+    u += __shfl_xor_sync(FULL, u, 2);
+    u += __shfl_xor_sync(FULL, u, 1);
+    return u;
+}
+
+template <int NT, int ELT>
 __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(const CSParams cp) {
     const KParams& p = cp.k;
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr int NW = NT / 32;
+    constexpr int RB = kCsMaxQ / NW;   // rows a warp in the dot pass, at most
+    static_assert(RB <= 8, "the dot pass reduces at most eight rows a warp");
     const int S = p.stages;
     const int q = p.q;
+    const int P = cp.groups;
+    const uint32_t stride = p.stage_stride;
     uint8_t* stages = smem;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * p.stage_stride);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * stride);
     uint64_t* empty = full + S;
     float4* meta = reinterpret_cast<float4*>(empty + S);
-    float* red = reinterpret_cast<float*>(meta + S);           // [kCsMaxQ][NW]
-    float4* grp = reinterpret_cast<float4*>(red + kCsMaxQ * NW);   // [NT / 16][16]
-    float* cvec = reinterpret_cast<float*>(grp + NT);            // [kCsMaxQ]
-    double* chk = reinterpret_cast<double*>(cvec + kCsMaxQ);    // [96]
-    float4* pbuf = reinterpret_cast<float4*>(chk + 96);         // [kCsProd][32] the producers' draws
+    float4* xs = meta + S;                                        // [XP]
+    float4* dpart = xs + (cp.chunk + 31) / 32 * 32;               // [P][chunk] when P > 1
+    float4* grp = dpart + (P > 1 ? (size_t)P * cp.chunk : 0);     // [NT / 16][16]
+    float2* rowc = reinterpret_cast<float2*>(grp + NT);           // [kCsMaxQ]
+    double* chk = reinterpret_cast<double*>(rowc + kCsMaxQ);      // [96]
+    float4* pbuf = reinterpret_cast<float4*>(chk + 96);           // [kCsProd][32] the producers' draws
     volatile Ctrl* ctrl = reinterpret_cast<volatile Ctrl*>(pbuf + 32 * kCsProd);
 
     const int tid = threadIdx.x;
@@ -184,7 +269,7 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
 
     {
         uint4* z = reinterpret_cast<uint4*>(stages);
-        const size_t nz = (size_t)S * p.stage_stride / 16;
+        const size_t nz = (size_t)S * stride / 16;
         for (size_t i = tid; i < nz; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -214,28 +299,22 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
 
     // ---------------- consumers ----------------
     const int rem = p.n & 3;
-    int tail_k = -1;   // k of the row's last slice for the thread that owns it (rem != 0)
-    {
-        const int lt = p.n4 - 1 - c0;   // local index of the last slice
-        if (rem && lt >= 0 && lt < nl && (lt % NT) == tid) tail_k = lt / NT;
-    }
-    float4 v[VPT];   // this CTA's chunk of x (the round's start point)
-    float4 d[VPT];   // the round's sum of c_j A_j over the chunk
-#pragma unroll
-    for (int k = 0; k < VPT; ++k) {
-        const int idx = tid + k * NT;
+    const bool has_tail = rem != 0 && nl > 0 && c0 + nl == p.n4;   // the row's last slice is this CTA's
+    // this CTA's chunk of x (the round's start point), zero past column n and past the chunk
+    for (int s = tid; s < (nl + 31) / 32 * 32; s += NT) {
         float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (idx < nl) {
-            const int j = (c0 + idx) * 4;
+        if (s < nl) {
+            const int j = (c0 + s) * 4;
             t.x = __ldg(p.x0 + j);
             if (j + 1 < p.n) t.y = __ldg(p.x0 + j + 1);
             if (j + 2 < p.n) t.z = __ldg(p.x0 + j + 2);
             if (j + 3 < p.n) t.w = __ldg(p.x0 + j + 3);
         }
-        v[k] = t;
-        d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        xs[s] = t;
     }
+    named_bar_sync(1, NT);
     const float rq = 1.0f / (float)q;
+    const int cnt = q > warp ? (q - warp + NW - 1) / NW : 0;   // rows j = warp, warp + NW, ... of this warp
     int64_t u = 0;                 // sequence index of the round's first row
     int s0 = 0;                    // its stage (u mod S) ...
     uint32_t ph0 = 0;              // ... and the parity of its pass over the ring
@@ -250,60 +329,42 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
     bool ok = true;
     for (int64_t r = 0; r < p.rounds && ok; ++r) {
         const int rb = (int)(r & 1);
-        // ---- 1. partial dots of the chunk, kCsGroup rows a pass ----
+        // ---- 1. partial dots: each warp forms its rows whole over the chunk ----
         bool got = true;
-        for (int j0 = 0; j0 < q; j0 += kCsGroup) {
-            const int cnt = min(kCsGroup, q - j0);
-            float acc[kCsGroup];
-            int sg[kCsGroup];
+        uint32_t off[RB];
 #pragma unroll
-            for (int rr = 0; rr < kCsGroup; ++rr) {
-                acc[rr] = 0.f;
-                sg[rr] = 0;
-                if (rr < cnt) {
-                    uint32_t par;
-                    sg[rr] = stage_of(j0 + rr, par);
-                    got = wait_parity(&full[sg[rr]], par, p.timeout_ns, status) && got;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-                const int idx = tid + k * NT;
-                const float4 xk = v[k];
-#pragma unroll
-                for (int rr = 0; rr < kCsGroup; ++rr) {
-                    if (rr < cnt) {
-                        const float4 a = cs_slice<ELT>(stages + (size_t)sg[rr] * p.stage_stride, idx, nl,
-                                                       k == tail_k, rem);
-                        float t = acc[rr];
-                        t = fmaf(a.x, xk.x, t);
-                        t = fmaf(a.y, xk.y, t);
-                        t = fmaf(a.z, xk.z, t);
-                        t = fmaf(a.w, xk.w, t);
-                        acc[rr] = t;
-                    }
-                }
-            }
-#pragma unroll
-            for (int rr = 0; rr < kCsGroup; ++rr) {
-#pragma unroll
-                for (int o = 16; o; o >>= 1) acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], o);
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int rr = 0; rr < kCsGroup; ++rr)
-                    if (rr < cnt) red[(j0 + rr) * NW + warp] = acc[rr];
+        for (int rr = 0; rr < RB; ++rr) {
+            off[rr] = 0;
+            if (rr < cnt) {
+                uint32_t par;
+                const int st = stage_of(warp + NW * rr, par);
+                got = cs_wait(&full[st], par, p.timeout_ns, status) && got;
+                off[rr] = (uint32_t)st * stride;
             }
         }
+        float acc[8];
+        switch (cnt) {
+            case 8: cs_dot_rows<ELT, (RB >= 8 ? 8 : RB)>(stages, off, xs, nl, has_tail, rem, acc); break;
+            case 7: cs_dot_rows<ELT, (RB >= 7 ? 7 : RB)>(stages, off, xs, nl, has_tail, rem, acc); break;
+            case 6: cs_dot_rows<ELT, (RB >= 6 ? 6 : RB)>(stages, off, xs, nl, has_tail, rem, acc); break;
+            case 5: cs_dot_rows<ELT, (RB >= 5 ? 5 : RB)>(stages, off, xs, nl, has_tail, rem, acc); break;
+            case 4: cs_dot_rows<ELT, (RB >= 4 ? 4 : RB)>(stages, off, xs, nl, has_tail, rem, acc); break;
+            case 3: cs_dot_rows<ELT, (RB >= 3 ? 3 : RB)>(stages, off, xs, nl, has_tail, rem, acc); break;
+            case 2: cs_dot_rows<ELT, 2>(stages, off, xs, nl, has_tail, rem, acc); break;
+            case 1: cs_dot_rows<ELT, 1>(stages, off, xs, nl, has_tail, rem, acc); break;
+            default:
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr) acc[rr] = 0.f;
+        }
+        {
+            const float sum = cs_reduce8(acc);
+            const int rr = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+            if ((lane & 3) == 0 && rr < cnt) cp.part[((size_t)rb * G + g) * kCsMaxQ + warp + NW * rr] = sum;
+        }
+        // ---- 2. one grid barrier (the CTA barrier orders every warp's partials before it) ----
         if (!bar_and(1, NT, got)) { ok = false; break; }
-        // ---- 2. this CTA's partials to global memory, one grid barrier ----
-        if (warp == 0) {
-            float* pg = cp.part + ((size_t)rb * G + g) * kCsMaxQ;
-            for (int j = lane; j < q; j += 32) pg[j] = cta_sum<NW>(red + j * NW);
-            named_bar_sync(2, 32);
-            if (lane == 0)
-                ctrl->flag = grid_sync(&p.info->bar_arrivals, nbar, (unsigned)G, status, p.timeout_ns) ? 1 : 0;
-        }
+        if (tid == 0)
+            ctrl->flag = grid_sync(&p.info->bar_arrivals, nbar, (unsigned)G, status, p.timeout_ns) ? 1 : 0;
         ++nbar;
         named_bar_sync(1, NT);
         if (!ctrl->flag) { ok = false; break; }
@@ -313,7 +374,7 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
         // the sum over h in ascending order: the same order in every CTA
         {
             constexpr int H = NT / 16;
-            constexpr int B = 16;   // loads in flight a thread (152 CTAs / 16 groups)
+            constexpr int B = 16;   // loads in flight a thread
             const int f = tid & 15, h = tid >> 4;
             const float4* pr4 = reinterpret_cast<const float4*>(cp.part + (size_t)rb * G * kCsMaxQ);
             float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -339,37 +400,50 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
             float dot = 0.f;
             for (int h = 0; h < NT / 16; ++h) dot += gj[h * 64];
             uint32_t par;
-            const float4 mb = meta[stage_of(j, par)];   // b_j, w_j / ||A_j||^2, row scale s_j
+            const int st = stage_of(j, par);
+            const float4 mb = meta[st];   // b_j, w_j / ||A_j||^2, row scale s_j
             // A_j = s_j q_j: <A_j, x> = s_j <q_j, x>, and the update takes (c_j s_j) q_j
-            cvec[j] = p.omega * (mb.x - mb.z * dot) * mb.y * mb.z;
+            rowc[j] = make_float2(p.omega * (mb.x - mb.z * dot) * mb.y * mb.z, __uint_as_float((uint32_t)st * stride));
         }
         named_bar_sync(1, NT);
-        // ---- 4. d = sum_j c_j A_j[chunk] in ascending j, then x += d / q ----
-        // UJ rows a step, their coefficients and slices loaded together
-        constexpr int UJ = VPT <= 2 ? 4 : (VPT <= 4 ? 2 : 1);
-        for (int j0 = 0; j0 < q; j0 += UJ) {
-            float c[UJ];
-            float4 a[UJ][VPT];
+        // ---- 4. d = sum_j c_j A_j[chunk], x += d / q ----
+        // item (pg, s): slice s summed over the rows j = pg, pg + P, ... (ascending);
+        // the P groups' sums then added in ascending pg
+        constexpr int UJ = 8;   // rows a step, their coefficients and slices loaded together
+        for (int it = tid; it < P * nl; it += NT) {
+            const int pg = it / nl, s = it - pg * nl;
+            float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
+            int j = pg;
+            for (; j + (UJ - 1) * P < q; j += UJ * P) {
+                float2 rc[UJ];
+                float4 a[UJ];
 #pragma unroll
-            for (int jj = 0; jj < UJ; ++jj) {
-                const int j = j0 + jj;
-                c[jj] = j < q ? cvec[j] : 0.f;
-                uint32_t par;
-                const uint8_t* stg = stages + (size_t)stage_of(j < q ? j : j0, par) * p.stage_stride;
+                for (int e = 0; e < UJ; ++e) rc[e] = rowc[j + e * P];
 #pragma unroll
-                for (int k = 0; k < VPT; ++k)
-                    a[jj][k] = j < q ? cs_slice<ELT>(stg, tid + k * NT, nl, k == tail_k, rem)
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+                for (int e = 0; e < UJ; ++e) a[e] = load4<ELT>(stages + __float_as_uint(rc[e].y), s);
 #pragma unroll
-            for (int jj = 0; jj < UJ; ++jj) {
-                const float2 c2 = make_float2(c[jj], c[jj]);
-#pragma unroll
-                for (int k = 0; k < VPT; ++k) {
-                    const float2 lo = __ffma2_rn(c2, make_float2(a[jj][k].x, a[jj][k].y), make_float2(d[k].x, d[k].y));
-                    const float2 hi = __ffma2_rn(c2, make_float2(a[jj][k].z, a[jj][k].w), make_float2(d[k].z, d[k].w));
-                    d[k] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                for (int e = 0; e < UJ; ++e) {
+                    const float2 c2 = make_float2(rc[e].x, rc[e].x);
+                    const float2 lo = __ffma2_rn(c2, make_float2(a[e].x, a[e].y), make_float2(dd.x, dd.y));
+                    const float2 hi = __ffma2_rn(c2, make_float2(a[e].z, a[e].w), make_float2(dd.z, dd.w));
+                    dd = make_float4(lo.x, lo.y, hi.x, hi.y);
                 }
+            }
+            for (; j < q; j += P) {
+                const float2 rc = rowc[j];
+                const float4 a = load4<ELT>(stages + __float_as_uint(rc.y), s);
+                const float2 c2 = make_float2(rc.x, rc.x);
+                const float2 lo = __ffma2_rn(c2, make_float2(a.x, a.y), make_float2(dd.x, dd.y));
+                const float2 hi = __ffma2_rn(c2, make_float2(a.z, a.w), make_float2(dd.z, dd.w));
+                dd = make_float4(lo.x, lo.y, hi.x, hi.y);
+            }
+            // the row's padding past column n never reaches x
+            if (has_tail && s == nl - 1) dd = zero_beyond(dd, rem);
+            if (P == 1) {
+                const float4 v = xs[s];
+                xs[s] = make_float4(fmaf(dd.x, rq, v.x), fmaf(dd.y, rq, v.y), fmaf(dd.z, rq, v.z), fmaf(dd.w, rq, v.w));
+            } else {
+                dpart[(size_t)pg * cp.chunk + s] = dd;
             }
         }
         __syncwarp();
@@ -381,34 +455,38 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
         u += q;
         s0 += q;
         if (s0 >= S) { s0 -= S; ph0 ^= 1u; }
-#pragma unroll
-        for (int k = 0; k < VPT; ++k) {
-            v[k] = make_float4(fmaf(d[k].x, rq, v[k].x), fmaf(d[k].y, rq, v[k].y), fmaf(d[k].z, rq, v[k].z),
-                               fmaf(d[k].w, rq, v[k].w));
-            d[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (P > 1) {
+            named_bar_sync(1, NT);
+            for (int s = tid; s < nl; s += NT) {
+                float4 dd = dpart[s];
+                for (int pg = 1; pg < P; ++pg) {
+                    const float4 t = dpart[(size_t)pg * cp.chunk + s];
+                    dd.x += t.x; dd.y += t.y; dd.z += t.z; dd.w += t.w;
+                }
+                const float4 v = xs[s];
+                xs[s] = make_float4(fmaf(dd.x, rq, v.x), fmaf(dd.y, rq, v.y), fmaf(dd.z, rq, v.z), fmaf(dd.w, rq, v.w));
+            }
         }
+        named_bar_sync(1, NT);   // x complete for the next round's dots
         // ---- 5. convergence / divergence check (a second grid barrier) ----
         const int64_t done = r + 1;
         const bool last = (done == p.rounds);
         const bool check = p.check_every > 0 && (done % p.check_every == 0 || last);
         if (check) {
             ChkAcc ca{0.f, 0.f, 0.f};
+            for (int s = tid; s < nl; s += NT) {
+                const int j = (c0 + s) * 4;
+                const float4 v = xs[s];
+                const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-                const int idx = tid + k * NT;
-                if (idx < nl) {
-                    const int j = (c0 + idx) * 4;
-                    const float vv[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (j + e < p.n) {
-                            ca.xx = fmaf(vv[e], vv[e], ca.xx);
-                            if (p.criterion == 1) {
-                                const float xr = __ldg(p.x_ref + j + e);
-                                const float dd = vv[e] - xr;
-                                ca.e2 = fmaf(dd, dd, ca.e2);
-                                ca.r2 = fmaf(xr, xr, ca.r2);
-                            }
+                for (int e = 0; e < 4; ++e) {
+                    if (j + e < p.n) {
+                        ca.xx = fmaf(vv[e], vv[e], ca.xx);
+                        if (p.criterion == 1) {
+                            const float xr = __ldg(p.x_ref + j + e);
+                            const float dd = vv[e] - xr;
+                            ca.e2 = fmaf(dd, dd, ca.e2);
+                            ca.r2 = fmaf(xr, xr, ca.r2);
                         }
                     }
                 }
@@ -446,34 +524,29 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
     }
     // stop the producer at what was consumed, and write this CTA's chunk of x
     if (tid == 0) ctrl->stop_t = u;
-#pragma unroll
-    for (int k = 0; k < VPT; ++k) {
-        const int idx = tid + k * NT;
-        if (idx < nl) {
-            const int j = (c0 + idx) * 4;
-            p.x[j] = v[k].x;
-            if (j + 1 < p.n) p.x[j + 1] = v[k].y;
-            if (j + 2 < p.n) p.x[j + 2] = v[k].z;
-            if (j + 3 < p.n) p.x[j + 3] = v[k].w;
-        }
+    named_bar_sync(1, NT);
+    for (int s = tid; s < nl; s += NT) {
+        const int j = (c0 + s) * 4;
+        const float4 v = xs[s];
+        p.x[j] = v.x;
+        if (j + 1 < p.n) p.x[j + 1] = v.y;
+        if (j + 2 < p.n) p.x[j + 2] = v.z;
+        if (j + 3 < p.n) p.x[j + 3] = v.w;
     }
 }
 
 typedef void (*CsKernelFn)(const CSParams);
 
 struct CsVariant {
-    int nt, vpt, elt;
+    int elt;
     CsKernelFn fn;
 };
 
-// 256 consumer threads whatever the chunk: the grid reduction of each round wants
-// many loads in flight, and idle threads cost nothing in the other phases
-#define CS_(NT, VPT, ELT) CsVariant{NT, VPT, ELT, rka_colsplit_kernel<NT, VPT, ELT>}
-static const CsVariant kCsTab[] = {
-    CS_(256, 1, ELT_F32),  CS_(256, 2, ELT_F32),  CS_(256, 4, ELT_F32),  CS_(256, 8, ELT_F32),
-    CS_(256, 1, ELT_BF16), CS_(256, 2, ELT_BF16), CS_(256, 4, ELT_BF16), CS_(256, 8, ELT_BF16),
-    CS_(256, 1, ELT_FP8),  CS_(256, 2, ELT_FP8),  CS_(256, 4, ELT_FP8),  CS_(256, 8, ELT_FP8),
-};
+// 256 consumer threads: eight rows a warp in the dot pass at 64 workers a round, and
+// the grid reduction of each round wants many loads in flight
+constexpr int kCsNT = 256;
+#define CS_(ELT) CsVariant{ELT, rka_colsplit_kernel<kCsNT, ELT>}
+static const CsVariant kCsTab[] = {CS_(ELT_F32), CS_(ELT_BF16), CS_(ELT_FP8)};
 #undef CS_
 
 int launch_colsplit_solve(const SolveArgs& a, const KParams& base, cudaStream_t st, int smem_max, int sms) {
@@ -482,20 +555,22 @@ int launch_colsplit_solve(const SolveArgs& a, const KParams& base, cudaStream_t 
     const int n4 = base.n4;
     const int chunk = ((n4 + sms - 1) / sms + 3) / 4 * 4;
     const int grid = (n4 + chunk - 1) / chunk;
-    const int nt = 256;
+    const int nt = kCsNT;
     const int elt = pl->dt == RK_F32 ? ELT_F32 : (pl->dt == RK_BF16 ? ELT_BF16 : ELT_FP8);
-    const CsVariant* var = nullptr;   // the fewest slices a thread that cover the chunk
+    const CsVariant* var = nullptr;
     for (const CsVariant& v : kCsTab)
-        if (v.nt == nt && v.elt == elt && v.vpt * nt >= chunk && (!var || v.vpt < var->vpt)) var = &v;
-    if (!var) return RK_EINVAL;   // rows beyond 8192 x 4 x SMs columns
+        if (v.elt == elt) var = &v;
+    if (!var) return RK_EINVAL;
+    // row groups of the update: as many as keep every consumer thread on a slice
+    const int P = nt / chunk > 1 ? (nt / chunk < a.q ? nt / chunk : a.q) : 1;
     const uint32_t eb = pl->dt == RK_F32 ? 4u : (pl->dt == RK_BF16 ? 2u : 1u);
     // a stage holds one chunk (the kernel reads no slice past the CTA's own)
     const uint32_t stride = ((uint32_t)chunk * 4u * eb + 127u) & ~127u;
     // every stage of a round stays taken until its update: at least q stages; up to
     // twice that lets the producer fetch the next round during the exchange
     int S = 0;
-    while (S < 2 * a.q + kCsGroup && S < 252 &&
-           (size_t)(S + 1) * stride + cs_ctrl_bytes(S + 1, nt) <= (size_t)smem_max)
+    while (S < 2 * a.q + kCsSpare && S < 252 &&
+           (size_t)(S + 1) * stride + cs_ctrl_bytes(S + 1, nt, chunk, P) <= (size_t)smem_max)
         ++S;
     S -= S % kCsProd;   // each producer warp serves its own stages
     if (S < a.q) return RK_EINVAL;   // the round's rows do not fit the shared memory
@@ -511,8 +586,9 @@ int launch_colsplit_solve(const SolveArgs& a, const KParams& base, cudaStream_t 
     cp.k.row_bytes = 0;   // per-CTA copy sizes are computed in the kernel
     cp.k.chkpart = a.V + ((part_floats + 3) & ~(size_t)3);
     cp.chunk = chunk;
+    cp.groups = P;
     cp.part = a.V;
-    const size_t smem = (size_t)S * stride + cs_ctrl_bytes(S, nt);
+    const size_t smem = (size_t)S * stride + cs_ctrl_bytes(S, nt, chunk, P);
     if (cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RK_ECUDA;
     void* args[] = {(void*)&cp};
