@@ -54,42 +54,34 @@ __device__ __forceinline__ uint32_t cs_copy_bytes(int nl) {
     return ((uint32_t)nl * 4u * eb + 15u) & ~15u;
 }
 
-// 16-byte asynchronous copy global -> shared (the L1-bypassing form), and the arrive on
-// an mbarrier that fires once this thread's earlier asynchronous copies have landed (the
-// barrier's expected count includes it: .noinc).
-__device__ __forceinline__ void cs_cp16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cs_cp_arrive(uint64_t* bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
 // Producer warps: rows of the q workers, round after round, into the ring (this
 // CTA's chunk of each row).  Sequence index u = round * q + j uses stage u mod S.
 // kCsProd warps share the rows: warp pw takes u = pw, pw + kCsProd, ... in order; S is
 // a multiple of kCsProd, so a stage is always filled by the same warp and its empty
 // barrier is at most one phase behind that warp's next use (the parity wait stays
-// unambiguous).  A warp draws 32 of its rows at once; then, row after row, the whole
-// warp copies the row's chunk in 16-byte pieces (consecutive lanes, consecutive pieces:
-// one 512-byte coalesced request an instruction) and every lane arrives on the stage's
-// full barrier when its pieces land; lane 0 also arrives after writing the row's b_i,
-// 1/||A_i||^2 and scale (the barrier expects 33 arrivals a phase).
+// unambiguous).  A warp draws 32 of its rows at once; then its lane 0, row after row,
+// writes the row's b_i, 1/||A_i||^2 and scale, arms the stage's full barrier with the
+// chunk's byte count and issues one bulk copy of the chunk (the barrier's phase
+// completes when the bytes have landed).
 template <int ELT>
 __device__ void cs_producer(const CSParams& cp, uint8_t* stages, uint64_t* full, uint64_t* empty,
                             float4* meta, volatile Ctrl* ctrl, float4* pbuf, int c0, int pw) {
     const KParams& p = cp.k;
     const int lane = threadIdx.x & 31;
     const int S = p.stages;
+    const int per = S / kCsProd;   // stages this warp fills
     const int q = p.q;
     const int64_t total = p.rounds * (int64_t)q;
     const int64_t mine = total > pw ? (total - pw + kCsProd - 1) / kCsProd : 0;   // rows of this warp
     constexpr uint32_t eb = ELT == ELT_F32 ? 4u : (ELT == ELT_BF16 ? 2u : 1u);
     const uint8_t* Ac = p.A + (size_t)c0 * 4u * eb;
     const int nl = max(0, min(p.n4 - c0, cp.chunk));
-    const int pieces = (int)(cs_copy_bytes<ELT>(nl) / 16u);
+    const uint32_t bytes = cs_copy_bytes<ELT>(nl);
+    const uint64_t pol = policy_evict_first();
     int* status = &p.info->status;
     int s = pw;               // stage of this warp's next row (S is a multiple of kCsProd)
     uint32_t pass = 0;
+    int64_t issued = 0;       // rows of this warp whose copies were issued
     bool stop = false;
     for (int64_t base = 0; base < mine && !stop; base += 32) {
         const int64_t il = base + lane;
@@ -108,47 +100,53 @@ __device__ void cs_producer(const CSParams& cp, uint8_t* stages, uint64_t* full,
             pbuf[lane] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row) * wi, sc);
         }
         __syncwarp();
-        const int64_t rem_ = mine - base;
-        const int cnt = rem_ < 32 ? (int)rem_ : 32;
-        for (int k = 0; k < cnt; ++k) {
-            const int64_t tt = (base + k) * kCsProd + pw;
-            bool go = tt < ctrl->stop_t;
-            if (go && tt >= S && lane == 0) {
-                // the previous copy into this stage (the last pass's) was consumed
-                const uint32_t prev = pass ^ 1u;
-                if (!mbar_try_wait(&empty[s], prev)) {
-                    const uint64_t t0 = globaltimer_ns();
-                    while (!mbar_try_wait(&empty[s], prev)) {
-                        // the ring is a round ahead: back off, leaving the issue slots and
-                        // the shared-memory pipe to the consumers
-                        __nanosleep(256);
-                        if (tt >= ctrl->stop_t) { go = false; break; }
-                        if (globaltimer_ns() - t0 > p.timeout_ns) {
-                            set_status(status, RK_ETIMEOUT);
-                            go = false;
-                            break;
+        if (lane == 0) {
+            const int64_t rem_ = mine - base;
+            const int cnt = rem_ < 32 ? (int)rem_ : 32;
+            for (int k = 0; k < cnt; ++k) {
+                const int64_t tt = (base + k) * kCsProd + pw;
+                if (tt >= ctrl->stop_t) { stop = true; break; }
+                if (tt >= S) {
+                    // the previous copy into this stage (the last pass's) was consumed
+                    const uint32_t prev = pass ^ 1u;
+                    if (!mbar_try_wait(&empty[s], prev)) {
+                        const uint64_t t0 = globaltimer_ns();
+                        while (!mbar_try_wait(&empty[s], prev)) {
+                            if (tt >= ctrl->stop_t) { stop = true; break; }
+                            if (globaltimer_ns() - t0 > p.timeout_ns) {
+                                set_status(status, RK_ETIMEOUT);
+                                stop = true;
+                                break;
+                            }
                         }
                     }
+                    if (stop) break;
                 }
-            }
-            go = __shfl_sync(0xffffffffu, go, 0);
-            if (!go) { stop = true; break; }
-            const float4 e = pbuf[k];
-            const uint8_t* src = Ac + (size_t)__float_as_uint(e.x) * (size_t)p.lda_bytes;
-            uint8_t* dst = stages + (size_t)s * p.stage_stride;
-            for (int pc = lane; pc < pieces; pc += 32) cs_cp16(dst + (size_t)pc * 16, src + (size_t)pc * 16);
-            cs_cp_arrive(&full[s]);
-            if (lane == 0) {
+                const float4 e = pbuf[k];
                 meta[s] = make_float4(e.y, e.z, e.w, 0.f);
-                mbar_arrive(&full[s]);
+                if (bytes) {
+                    mbar_arrive_expect_tx(&full[s], bytes);
+                    bulk_g2s(stages + (size_t)s * p.stage_stride, Ac + (size_t)__float_as_uint(e.x) * (size_t)p.lda_bytes,
+                             bytes, &full[s], pol);
+                } else {
+                    mbar_arrive(&full[s]);
+                }
+                issued = base + k + 1;
+                s += kCsProd;
+                if (s >= S) { s -= S; pass ^= 1u; }
             }
-            s += kCsProd;
-            if (s >= S) { s -= S; pass ^= 1u; }
         }
+        stop = __shfl_sync(0xffffffffu, stop, 0);
         __syncwarp();
     }
-    // every copy this warp issued must land before the CTA exits
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    // every copy this warp issued must land before the CTA exits: the last fill of
+    // each of its stages
+    if (lane == 0) {
+        for (int64_t il = issued > per ? issued - per : 0; il < issued; ++il) {
+            const int st = pw + kCsProd * (int)(il % per);
+            wait_parity(&full[st], (uint32_t)((il / per) & 1), drain_limit_ns(p.timeout_ns), status);
+        }
+    }
     __syncwarp();
 }
 
@@ -275,7 +273,7 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
-            mbar_init(&full[i], 33);   // 32 copying lanes + lane 0's row data
+            mbar_init(&full[i], 1);    // lane 0's arrive with the copy's byte count
             mbar_init(&empty[i], NW);
         }
         ctrl->stop_t = total;
