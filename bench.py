@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--omega", default="1",
                     help="relaxation of the timed solve: a number, or 'star' for alpha* of "
                          "Eq. (best_alpha) from the GPU spectrum estimate (computed before timing)")
+    ap.add_argument("--adjoint-q-t", type=int, default=40,
+                    help="workers a round of the adjoint workload's minimum-norm solve on A^T")
+    ap.add_argument("--adjoint-rounds-t", type=int, default=15000,
+                    help="rounds of the adjoint workload's minimum-norm solve on A^T")
     ap.add_argument("--workload", default="consistent",
                     choices=["consistent", "lsq", "precision", "horizon", "adjoint", "adjoint-c5",
                              "setup", "rounds"],
@@ -1191,8 +1195,9 @@ def run_adjoint_large(args, rk, dev):
     """Differentiation form at 200000 x 20000 (b = A x* + N(0, 1e-3^2), L = 0.5||x - x_t||^2)
     through torch.autograd, as at 50000 x 5000: forward RKA with 32 workers per SM and a
     decreasing relaxation, backward (A^T copy and its plan, the minimum-norm solve on A^T
-    by 16-CTA cluster workers with rows of 800 KB, the RKA solve of A g = y, the residual
-    and the 16 GB rank-2 gradient of A), timed after one untimed pass.  Reported with the
+    by RKA with x split by columns over the grid (rows of 800 KB, 40 workers, alpha* of
+    Eq. (best_alpha) from A's spectrum), the RKA solve of A g = y, the residual and the
+    16 GB rank-2 gradient of A), timed after one untimed pass.  Reported with the
     times: ||x - x_LS|| / ||x_LS|| (x_LS by FP64 CGLS, a measurement reference) and the
     relative residuals of both backward solves, ||A^T y - dL/dx|| / ||dL/dx|| and
     ||A g - y|| / ||y|| (FP64-class, rk_residual)."""
@@ -1204,12 +1209,16 @@ def run_adjoint_large(args, rk, dev):
     xt = torch.randn(n, generator=torch.Generator(device=dev).manual_seed(5), device=dev)
     qa = 32 * sms_of(dev)
     plan = rk.rk_setup(A)
-    w, _ = rk.optimal_weight(A, qa, k=2, plan=plan)
+    w, sp = rk.optimal_weight(A, qa, k=2, plan=plan)
     fracs = ((1.0, 150), (0.1, 400), (0.01, 2000))
     sched = tuple((w * f, r) for f, r in fracs)
-    rounds_t, alpha_t, omega_t, rounds_g = 60, 4000, 2.0, 300
-    cfg = rk.AdjointConfig(q=qa, alpha=1, rounds=rounds_g, omega=w, q_t=6, cluster_size_t=16,
-                           alpha_t=alpha_t, rounds_t=rounds_t, omega_t=omega_t, seed=args.seed + 1)
+    # the rows of A^T have A's nonzero singular values: Eq. (best_alpha) with A's s_min, s_max
+    q_t = args.adjoint_q_t
+    rounds_t, rounds_g = args.adjoint_rounds_t, 300
+    omega_t = rk.alpha_star(q_t, sp.s_min, sp.s_max)
+    cfg = rk.AdjointConfig(q=qa, alpha=1, rounds=rounds_g, omega=w, q_t=q_t, cluster_size_t=0,
+                           alpha_t=1, rounds_t=rounds_t, omega_t=omega_t, seed=args.seed + 1,
+                           check_every=50)
     Ar = A.requires_grad_(True)
     br = b.requires_grad_(True)
     times = []
@@ -1240,8 +1249,9 @@ def run_adjoint_large(args, rk, dev):
         "forward": {"method": f"RKA q={qa}, weights alpha* x " + ", ".join(f"{f:g} ({r} rounds)" for f, r in fracs),
                     "ms": round(t_fwd, 2)},
         "backward_ms": round(t_bwd, 2),
-        "y_solve": {"on": "A^T (20000 rows of 200000)", "q": 6, "cluster": 16, "alpha": alpha_t,
-                    "rounds": rounds_t, "omega": omega_t, "relative_residual": res_t},
+        "y_solve": {"on": "A^T (20000 rows of 200000)", "method": "RKA, x split by columns over the grid",
+                    "q": q_t, "alpha": 1, "rounds": rounds_t, "omega": round(omega_t, 3),
+                    "relative_residual": res_t},
         "g_solve": {"q": qa, "alpha": 1, "rounds": rounds_g, "omega": round(w, 2)},
         "x_rel_err_vs_x_ls": float((xd.double() - x_ls).norm() / x_ls.norm()),
         "x_ls_reference": f"FP64 CGLS ({t_cgls:.1f} s)",
