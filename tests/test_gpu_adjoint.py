@@ -1,7 +1,8 @@
 """Differentiation form on the GPU: transpose, rank-2 gradient, the
-minimum-norm solve on A^T against the oracle (same draws), the whole adjoint at
-the GPU's forward point against the FP64 QR adjoint at that point, and the
-autograd gradient against central finite differences of the FP64 map."""
+minimum-norm solve on A^T against the oracle (same draws; one-CTA workers, and x split by
+columns over the grid for rows of A^T too long for one CTA), the whole adjoint at the
+GPU's forward point against the FP64 QR adjoint at that point (both solve layouts), and
+the autograd gradient against central finite differences of the FP64 map."""
 import numpy as np
 import pytest
 
@@ -72,6 +73,42 @@ def test_adjoint_at_forward_point_matches_qr(rk, inc):
     s, xt, A, plan = inc
     x, _ = rk.rkab_solve(plan, _dev(s.b), q=8, alpha=200, rounds=60, seed=3, check_every=0)
     cfg = rk.AdjointConfig(q=8, alpha_t=200, rounds_t=80, alpha=200, rounds=80, seed=5)
+    gx = x - _dev(xt)
+    gA, gb, g = rk.Adjoint(plan, cfg).backward(_dev(s.b), x, gx)
+    rA, rb, rg = oracle.lstsq_adjoint(s.A, s.b, x.cpu().numpy(), xt)
+    assert_close(gb.cpu().numpy(), rb, TOL)
+    assert_close(g.cpu().numpy(), rg, TOL)
+    assert_close(gA.cpu().numpy(), rA, TOL)
+
+
+def test_min_norm_solve_column_split_matches_oracle(rk):
+    """The y-solve on rows of A^T too long for one CTA (100 x 50000: 200 KB rows) runs RKA
+    with x split by columns over the grid (the kernel of the timed adjoints): the same
+    draws of stream 1 as the oracle, relaxation omega_t, every element within 1e-4."""
+    s = rk_inputs.gaussian_system(50000, 100, seed=87, noise=1e-3)
+    xt = rk_inputs.target_vector(100, seed=87)
+    plan = rk.rk_setup(_dev(s.A))
+    cfg = rk.AdjointConfig(q=4, alpha_t=1, q_t=32, rounds_t=12, omega_t=20.0, alpha=100, rounds=1, seed=7)
+    adj = rk.Adjoint(plan, cfg)
+    x = torch.zeros(100, device="cuda")
+    _, gb, _ = adj.backward(_dev(s.b), x, _dev(xt) * -1.0)
+    At = np.ascontiguousarray(s.A.T)
+    yo = oracle.rkab(At, -xt.astype(np.float64), np.zeros(50000), q=32, alpha=1, rounds=12, seed=7,
+                     tab=oracle.table(At), stream=1, omega=20.0)
+    assert_close(gb.cpu().numpy(), yo, TOL)
+
+
+def test_adjoint_column_split_at_forward_point_matches_qr(rk):
+    """40000 x 48 (A^T rows of 160 KB: the column-split minimum-norm solve with alpha* of
+    Eq. (best_alpha) from A's spectrum): the whole adjoint at the GPU's forward point against
+    the FP64 QR adjoint evaluated there."""
+    s = rk_inputs.gaussian_system(40000, 48, seed=89, noise=1e-3)
+    xt = rk_inputs.target_vector(48, seed=89)
+    plan = rk.rk_setup(_dev(s.A))
+    x, _ = rk.rkab_solve(plan, _dev(s.b), q=8, alpha=48, rounds=80, seed=3, check_every=0)
+    lmin, lmax, fro2 = oracle.spectrum(s.A)
+    om = float(oracle.alpha_star(48, lmin / fro2, lmax / fro2))
+    cfg = rk.AdjointConfig(q=8, alpha=48, rounds=80, alpha_t=1, q_t=48, rounds_t=150, omega_t=om, seed=5)
     gx = x - _dev(xt)
     gA, gb, g = rk.Adjoint(plan, cfg).backward(_dev(s.b), x, gx)
     rA, rb, rg = oracle.lstsq_adjoint(s.A, s.b, x.cpu().numpy(), xt)
