@@ -39,11 +39,12 @@ struct CSParams {
 // xs[XP] float4 (this CTA's chunk of x, XP = chunk rounded up to 32 slices),
 // dpart[P][chunk] float4 (the update's group sums, P > 1 only), grp[NT / 16][16]
 // float4 (partial sums of the grid reduction), rowc[kCsMaxQ] float2 (c_j and row j's
-// stage offset), chk[96] double, pbuf[kCsProd][32] float4, Ctrl.
+// stage offset), chk[96] double, pbuf[kCsProd][32] float4, Ctrl (16 bytes), fillpar[S]
+// bytes (the parity of each stage's last fill, for the producers' drain).
 __host__ __device__ inline size_t cs_ctrl_bytes(int S, int nt, int chunk, int P) {
     const size_t xp = (size_t)(chunk + 31) / 32 * 32;
     return (size_t)S * 32 + xp * 16 + (P > 1 ? (size_t)P * chunk * 16 : 0) + (size_t)nt * 16 + kCsMaxQ * 8 +
-           96 * 8 + kCsProd * 32 * 16 + 64;
+           96 * 8 + kCsProd * 32 * 16 + 16 + ((size_t)S + 15) / 16 * 16 + 64;
 }
 
 // Bytes of this CTA's chunk of a row: nl slices of 4 elements, rounded up to 16 bytes
@@ -54,18 +55,31 @@ __device__ __forceinline__ uint32_t cs_copy_bytes(int nl) {
     return ((uint32_t)nl * 4u * eb + 15u) & ~15u;
 }
 
+// Non-blocking test of an mbarrier phase (mbarrier.test_wait: returns at once).
+__device__ __forceinline__ bool cs_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Producer warps: rows of the q workers, round after round, into the ring (this
 // CTA's chunk of each row).  Sequence index u = round * q + j uses stage u mod S.
 // kCsProd warps share the rows: warp pw takes u = pw, pw + kCsProd, ... in order; S is
 // a multiple of kCsProd, so a stage is always filled by the same warp and its empty
 // barrier is at most one phase behind that warp's next use (the parity wait stays
-// unambiguous).  A warp draws 32 of its rows at once; then its lane 0, row after row,
-// writes the row's b_i, 1/||A_i||^2 and scale, arms the stage's full barrier with the
-// chunk's byte count and issues one bulk copy of the chunk (the barrier's phase
-// completes when the bytes have landed).
+// unambiguous).  A warp draws 32 of its rows at once; then for each row a lane writes
+// the row's b_i, 1/||A_i||^2 and scale, arms the stage's full barrier with the chunk's
+// byte count and issues one bulk copy of the chunk (the barrier's phase completes when
+// the bytes have landed), and records the fill's parity in fillpar[stage].
 template <int ELT>
 __device__ void cs_producer(const CSParams& cp, uint8_t* stages, uint64_t* full, uint64_t* empty,
-                            float4* meta, volatile Ctrl* ctrl, float4* pbuf, int c0, int pw) {
+                            float4* meta, volatile Ctrl* ctrl, float4* pbuf, uint8_t* fillpar, int c0, int pw) {
     const KParams& p = cp.k;
     const int lane = threadIdx.x & 31;
     const int S = p.stages;
@@ -79,9 +93,9 @@ __device__ void cs_producer(const CSParams& cp, uint8_t* stages, uint64_t* full,
     const uint32_t bytes = cs_copy_bytes<ELT>(nl);
     const uint64_t pol = policy_evict_first();
     int* status = &p.info->status;
-    int s = pw;               // stage of this warp's next row (S is a multiple of kCsProd)
-    uint32_t pass = 0;
-    int64_t issued = 0;       // rows of this warp whose copies were issued
+    // rows issued at once: small chunks are bound by the copies' count (issue them together),
+    // large ones by bandwidth (issue them in order, so that the first rows land first)
+    const int lanes = bytes > 4096u ? 1 : (per < 32 ? per : 32);
     bool stop = false;
     for (int64_t base = 0; base < mine && !stop; base += 32) {
         const int64_t il = base + lane;
@@ -100,18 +114,22 @@ __device__ void cs_producer(const CSParams& cp, uint8_t* stages, uint64_t* full,
             pbuf[lane] = make_float4(__uint_as_float(row), __ldg(p.b + row), __ldg(p.inv + row) * wi, sc);
         }
         __syncwarp();
-        if (lane == 0) {
-            const int64_t rem_ = mine - base;
-            const int cnt = rem_ < 32 ? (int)rem_ : 32;
-            for (int k = 0; k < cnt; ++k) {
-                const int64_t tt = (base + k) * kCsProd + pw;
-                if (tt >= ctrl->stop_t) { stop = true; break; }
-                if (tt >= S) {
-                    // the previous copy into this stage (the last pass's) was consumed
-                    const uint32_t prev = pass ^ 1u;
-                    if (!mbar_try_wait(&empty[s], prev)) {
+        // ... and issue them
+        const int64_t rem_ = mine - base;
+        const int cnt = rem_ < 32 ? (int)rem_ : 32;
+        if (lanes == 1) {
+            // in order, from lane 0, waiting for each stage in turn
+            if (lane == 0) {
+                for (int k = 0; k < cnt; ++k) {
+                    const int64_t il = base + k;
+                    const int64_t tt = il * kCsProd + pw;
+                    const int st = pw + kCsProd * (int)(il % per);
+                    const uint32_t ps = (uint32_t)((il / per) & 1);
+                    if (tt >= ctrl->stop_t) { stop = true; break; }
+                    if (tt >= S && !mbar_try_wait(&empty[st], ps ^ 1u)) {
+                        // the previous copy into this stage (the last pass's) was consumed
                         const uint64_t t0 = globaltimer_ns();
-                        while (!mbar_try_wait(&empty[s], prev)) {
+                        while (!mbar_try_wait(&empty[st], ps ^ 1u)) {
                             if (tt >= ctrl->stop_t) { stop = true; break; }
                             if (globaltimer_ns() - t0 > p.timeout_ns) {
                                 set_status(status, RK_ETIMEOUT);
@@ -119,33 +137,81 @@ __device__ void cs_producer(const CSParams& cp, uint8_t* stages, uint64_t* full,
                                 break;
                             }
                         }
+                        if (stop) break;
                     }
-                    if (stop) break;
+                    const float4 e = pbuf[k];
+                    meta[st] = make_float4(e.y, e.z, e.w, 0.f);
+                    if (bytes) {
+                        mbar_arrive_expect_tx(&full[st], bytes);
+                        bulk_g2s(stages + (size_t)st * p.stage_stride,
+                                 Ac + (size_t)__float_as_uint(e.x) * (size_t)p.lda_bytes, bytes, &full[st], pol);
+                    } else {
+                        mbar_arrive(&full[st]);
+                    }
+                    fillpar[st] = (uint8_t)ps;
                 }
-                const float4 e = pbuf[k];
-                meta[s] = make_float4(e.y, e.z, e.w, 0.f);
-                if (bytes) {
-                    mbar_arrive_expect_tx(&full[s], bytes);
-                    bulk_g2s(stages + (size_t)s * p.stage_stride, Ac + (size_t)__float_as_uint(e.x) * (size_t)p.lda_bytes,
-                             bytes, &full[s], pol);
-                } else {
-                    mbar_arrive(&full[s]);
-                }
-                issued = base + k + 1;
-                s += kCsProd;
-                if (s >= S) { s -= S; pass ^= 1u; }
             }
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            __syncwarp();
+            continue;
         }
-        stop = __shfl_sync(0xffffffffu, stop, 0);
+        // up to `lanes` <= `per` rows at once (distinct stages, each stage's empty barrier
+        // at most one phase behind): every lane tests its own stage without blocking and
+        // issues its copy when the stage is free; when none is free, the lane of the
+        // oldest pending row (whose stage is released first) blocks on it alone
+        for (int k0 = 0; k0 < cnt && !stop; k0 += lanes) {
+            const int k = k0 + lane;
+            const int64_t il = base + k;
+            const int64_t tt = il * kCsProd + pw;
+            const int st = pw + kCsProd * (int)(il % per);
+            const uint32_t ps = (uint32_t)((il / per) & 1);
+            bool pending = lane < lanes && k < cnt;
+            while (__any_sync(0xffffffffu, pending)) {
+                if (pending && tt >= ctrl->stop_t) {   // past what the consumers take
+                    pending = false;
+                    stop = true;
+                }
+                const bool ready = pending && (tt < S || cs_test_wait(&empty[st], ps ^ 1u));
+                if (ready) {
+                    const float4 e = pbuf[k];
+                    meta[st] = make_float4(e.y, e.z, e.w, 0.f);
+                    if (bytes) {
+                        mbar_arrive_expect_tx(&full[st], bytes);
+                        bulk_g2s(stages + (size_t)st * p.stage_stride,
+                                 Ac + (size_t)__float_as_uint(e.x) * (size_t)p.lda_bytes, bytes, &full[st], pol);
+                    } else {
+                        mbar_arrive(&full[st]);
+                    }
+                    fillpar[st] = (uint8_t)ps;
+                    pending = false;
+                }
+                const unsigned waiting = __ballot_sync(0xffffffffu, pending);
+                if (waiting && !__any_sync(0xffffffffu, ready)) {
+                    if (lane == __ffs(waiting) - 1) {
+                        // the previous copy into this stage (the last pass's) was consumed
+                        const uint64_t t0 = globaltimer_ns();
+                        while (!mbar_try_wait(&empty[st], ps ^ 1u)) {
+                            if (tt >= ctrl->stop_t) break;
+                            if (globaltimer_ns() - t0 > p.timeout_ns) {
+                                set_status(status, RK_ETIMEOUT);
+                                stop = true;
+                                break;
+                            }
+                        }
+                    }
+                    if (__any_sync(0xffffffffu, stop)) pending = false;   // a wait that ran out
+                }
+            }
+            stop = __any_sync(0xffffffffu, stop);
+        }
         __syncwarp();
     }
     // every copy this warp issued must land before the CTA exits: the last fill of
     // each of its stages
-    if (lane == 0) {
-        for (int64_t il = issued > per ? issued - per : 0; il < issued; ++il) {
-            const int st = pw + kCsProd * (int)(il % per);
-            wait_parity(&full[st], (uint32_t)((il / per) & 1), drain_limit_ns(p.timeout_ns), status);
-        }
+    __syncwarp();
+    for (int i = lane; i < per; i += 32) {
+        const int st = pw + kCsProd * i;
+        if (fillpar[st] != 0xFFu) wait_parity(&full[st], fillpar[st], drain_limit_ns(p.timeout_ns), status);
     }
     __syncwarp();
 }
@@ -255,6 +321,7 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
     double* chk = reinterpret_cast<double*>(rowc + kCsMaxQ);      // [96]
     float4* pbuf = reinterpret_cast<float4*>(chk + 96);           // [kCsProd][32] the producers' draws
     volatile Ctrl* ctrl = reinterpret_cast<volatile Ctrl*>(pbuf + 32 * kCsProd);
+    uint8_t* fillpar = reinterpret_cast<uint8_t*>(pbuf + 32 * kCsProd) + 16;   // [S] parity of each stage's last fill
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -273,8 +340,9 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
-            mbar_init(&full[i], 1);    // lane 0's arrive with the copy's byte count
+            mbar_init(&full[i], 1);    // the issuing lane's arrive with the copy's byte count
             mbar_init(&empty[i], NW);
+            fillpar[i] = 0xFFu;        // never filled
         }
         ctrl->stop_t = total;
         ctrl->flag = 0;
@@ -291,7 +359,7 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
     }
     if (warp >= NW) {
         const int pw = warp - NW;
-        cs_producer<ELT>(cp, stages, full, empty, meta, ctrl, pbuf + 32 * pw, c0, pw);
+        cs_producer<ELT>(cp, stages, full, empty, meta, ctrl, pbuf + 32 * pw, fillpar, c0, pw);
         return;
     }
 
