@@ -14,9 +14,9 @@
 //   3. every CTA sums the G partials of each row in the same fixed order,
 //      <A_j, x> = sum_g p_j^g, and forms c_j = omega w_j (b_j - <A_j, x>) / ||A_j||^2;
 //   4. d = sum_j c_j A_j[chunk g], x[chunk g] += d / q: the average of the q
-//      projections of Eq. (rka_uni_weights), held in the difference form (the rows
-//      split into P groups so that every thread has slices to sum; the group sums
-//      added in a fixed order).
+//      projections of Eq. (rka_uni_weights), held in the difference form (for chunks
+//      of at most 128 slices each warp sums its own rows and the warp sums are added
+//      in a fixed order; beyond, each thread sums its slices over all rows).
 // The stages of a round are released after step 4, so the ring holds at least the
 // round's q rows; the producer fills the rest with the next round's rows. Checks
 // (criterion, divergence) add a second grid barrier on the rounds they run.
@@ -27,23 +27,25 @@ namespace rk {
 constexpr int kCsMaxQ = 64;    // workers a round (colsplit_fits in rk_internal.h)
 constexpr int kCsSpare = 8;    // ring stages beyond two rounds' rows
 constexpr int kCsProd = 4;     // producer warps (the ring's stage count is a multiple)
+constexpr int kCsWarpRowsL = 4;   // slices a lane in the warp-rows update (chunks <= 128 slices)
 
 struct CSParams {
     KParams k;
     int chunk;          // slices (4 elements) of x per CTA, a multiple of 4
-    int groups;         // P: row groups of the update (P x chunk <= consumer threads, or 1)
+    int warp_rows;      // 1: the update takes a warp's own rows (chunks of at most
+                        // kCsWarpRowsL * 32 slices); 0: a thread's slices over all rows
     float* part;        // [2][G][kCsMaxQ] partial dots (round parity, CTA, worker)
 };
 
 // Shared memory after the stages: full[S] + empty[S] mbarriers, meta[S] float4,
 // xs[XP] float4 (this CTA's chunk of x, XP = chunk rounded up to 32 slices),
-// dpart[P][chunk] float4 (the update's group sums, P > 1 only), grp[NT / 16][16]
+// dpart[NW][chunk] float4 (the update's warp sums, warp-rows mode only), grp[NT / 16][16]
 // float4 (partial sums of the grid reduction), rowc[kCsMaxQ] float2 (c_j and row j's
 // stage offset), chk[96] double, pbuf[kCsProd][32] float4, Ctrl (16 bytes), fillpar[S]
 // bytes (the parity of each stage's last fill, for the producers' drain).
-__host__ __device__ inline size_t cs_ctrl_bytes(int S, int nt, int chunk, int P) {
+__host__ __device__ inline size_t cs_ctrl_bytes(int S, int nt, int chunk, bool warp_rows) {
     const size_t xp = (size_t)(chunk + 31) / 32 * 32;
-    return (size_t)S * 32 + xp * 16 + (P > 1 ? (size_t)P * chunk * 16 : 0) + (size_t)nt * 16 + kCsMaxQ * 8 +
+    return (size_t)S * 32 + xp * 16 + (warp_rows ? (size_t)(nt / 32) * chunk * 16 : 0) + (size_t)nt * 16 + kCsMaxQ * 8 +
            96 * 8 + kCsProd * 32 * 16 + 16 + ((size_t)S + 15) / 16 * 16 + 64;
 }
 
@@ -308,15 +310,15 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
     static_assert(RB <= 8, "the dot pass reduces at most eight rows a warp");
     const int S = p.stages;
     const int q = p.q;
-    const int P = cp.groups;
+    const bool warp_rows = cp.warp_rows != 0;
     const uint32_t stride = p.stage_stride;
     uint8_t* stages = smem;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * stride);
     uint64_t* empty = full + S;
     float4* meta = reinterpret_cast<float4*>(empty + S);
     float4* xs = meta + S;                                        // [XP]
-    float4* dpart = xs + (cp.chunk + 31) / 32 * 32;               // [P][chunk] when P > 1
-    float4* grp = dpart + (P > 1 ? (size_t)P * cp.chunk : 0);     // [NT / 16][16]
+    float4* dpart = xs + (cp.chunk + 31) / 32 * 32;               // [NW][chunk] with warp rows
+    float4* grp = dpart + (warp_rows ? (size_t)NW * cp.chunk : 0);   // [NT / 16][16]
     float2* rowc = reinterpret_cast<float2*>(grp + NT);           // [kCsMaxQ]
     double* chk = reinterpret_cast<double*>(rowc + kCsMaxQ);      // [96]
     float4* pbuf = reinterpret_cast<float4*>(chk + 96);           // [kCsProd][32] the producers' draws
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
             mbar_init(&full[i], 1);    // the issuing lane's arrive with the copy's byte count
-            mbar_init(&empty[i], NW);
+            mbar_init(&empty[i], warp_rows ? 1 : NW);   // the readers of a stage's row
             fillpar[i] = 0xFFu;        // never filled
         }
         ctrl->stop_t = total;
@@ -473,66 +475,93 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
         }
         named_bar_sync(1, NT);
         // ---- 4. d = sum_j c_j A_j[chunk], x += d / q ----
-        // item (pg, s): slice s summed over the rows j = pg, pg + P, ... (ascending);
-        // the P groups' sums then added in ascending pg
-        constexpr int UJ = 8;   // rows a step, their coefficients and slices loaded together
-        for (int it = tid; it < P * nl; it += NT) {
-            const int pg = it / nl, s = it - pg * nl;
-            float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
-            int j = pg;
-            for (; j + (UJ - 1) * P < q; j += UJ * P) {
-                float2 rc[UJ];
-                float4 a[UJ];
+        if (warp_rows) {
+            // warp w sums its own rows j = w, w + NW, ... (ascending) over the chunk's
+            // slices lane + 32 i into dpart[w]; the NW sums are then added in ascending w
+            float2 rc[8];
 #pragma unroll
-                for (int e = 0; e < UJ; ++e) rc[e] = rowc[j + e * P];
+            for (int rr = 0; rr < 8; ++rr) rc[rr] = rr < cnt ? rowc[warp + NW * rr] : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int e = 0; e < UJ; ++e) a[e] = load4<ELT>(stages + __float_as_uint(rc[e].y), s);
+            for (int i = 0; i < kCsWarpRowsL; ++i) {
+                const int sl = lane + 32 * i;
+                if (sl < nl) {
+                    float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int e = 0; e < UJ; ++e) {
-                    const float2 c2 = make_float2(rc[e].x, rc[e].x);
-                    const float2 lo = __ffma2_rn(c2, make_float2(a[e].x, a[e].y), make_float2(dd.x, dd.y));
-                    const float2 hi = __ffma2_rn(c2, make_float2(a[e].z, a[e].w), make_float2(dd.z, dd.w));
-                    dd = make_float4(lo.x, lo.y, hi.x, hi.y);
+                    for (int rr = 0; rr < 8; ++rr) {
+                        if (rr < cnt) {
+                            const float4 av = load4<ELT>(stages + __float_as_uint(rc[rr].y), sl);
+                            const float2 c2 = make_float2(rc[rr].x, rc[rr].x);
+                            const float2 lo = __ffma2_rn(c2, make_float2(av.x, av.y), make_float2(dd.x, dd.y));
+                            const float2 hi = __ffma2_rn(c2, make_float2(av.z, av.w), make_float2(dd.z, dd.w));
+                            dd = make_float4(lo.x, lo.y, hi.x, hi.y);
+                        }
+                    }
+                    // the row's padding past column n never reaches x
+                    if (has_tail && sl == nl - 1) dd = zero_beyond(dd, rem);
+                    dpart[(size_t)warp * cp.chunk + sl] = dd;
                 }
             }
-            for (; j < q; j += P) {
-                const float2 rc = rowc[j];
-                const float4 a = load4<ELT>(stages + __float_as_uint(rc.y), s);
-                const float2 c2 = make_float2(rc.x, rc.x);
-                const float2 lo = __ffma2_rn(c2, make_float2(a.x, a.y), make_float2(dd.x, dd.y));
-                const float2 hi = __ffma2_rn(c2, make_float2(a.z, a.w), make_float2(dd.z, dd.w));
-                dd = make_float4(lo.x, lo.y, hi.x, hi.y);
+            __syncwarp();
+            // this warp alone read its rows' stages: release them
+            if (lane < cnt) {
+                uint32_t par;
+                mbar_arrive(&empty[stage_of(warp + NW * lane, par)]);
             }
-            // the row's padding past column n never reaches x
-            if (has_tail && s == nl - 1) dd = zero_beyond(dd, rem);
-            if (P == 1) {
-                const float4 v = xs[s];
-                xs[s] = make_float4(fmaf(dd.x, rq, v.x), fmaf(dd.y, rq, v.y), fmaf(dd.z, rq, v.z), fmaf(dd.w, rq, v.w));
-            } else {
-                dpart[(size_t)pg * cp.chunk + s] = dd;
+            named_bar_sync(1, NT);
+            for (int sl = tid; sl < nl; sl += NT) {
+                float4 dd = dpart[sl];
+#pragma unroll
+                for (int w = 1; w < NW; ++w) {
+                    const float4 t = dpart[(size_t)w * cp.chunk + sl];
+                    dd.x += t.x; dd.y += t.y; dd.z += t.z; dd.w += t.w;
+                }
+                const float4 v = xs[sl];
+                xs[sl] = make_float4(fmaf(dd.x, rq, v.x), fmaf(dd.y, rq, v.y), fmaf(dd.z, rq, v.z), fmaf(dd.w, rq, v.w));
             }
-        }
-        __syncwarp();
-        // this warp's release of the round's stages, one lane a stage
-        for (int j = lane; j < q; j += 32) {
-            uint32_t par;
-            mbar_arrive(&empty[stage_of(j, par)]);
+        } else {
+            // slice s of every thread summed over all rows in ascending j, UJ rows a step
+            // with their coefficients and slices loaded together
+            constexpr int UJ = 8;
+            for (int sl = tid; sl < nl; sl += NT) {
+                float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
+                int j = 0;
+                for (; j + UJ <= q; j += UJ) {
+                    float2 rcj[UJ];
+                    float4 av[UJ];
+#pragma unroll
+                    for (int e = 0; e < UJ; ++e) rcj[e] = rowc[j + e];
+#pragma unroll
+                    for (int e = 0; e < UJ; ++e) av[e] = load4<ELT>(stages + __float_as_uint(rcj[e].y), sl);
+#pragma unroll
+                    for (int e = 0; e < UJ; ++e) {
+                        const float2 c2 = make_float2(rcj[e].x, rcj[e].x);
+                        const float2 lo = __ffma2_rn(c2, make_float2(av[e].x, av[e].y), make_float2(dd.x, dd.y));
+                        const float2 hi = __ffma2_rn(c2, make_float2(av[e].z, av[e].w), make_float2(dd.z, dd.w));
+                        dd = make_float4(lo.x, lo.y, hi.x, hi.y);
+                    }
+                }
+                for (; j < q; ++j) {
+                    const float2 rcj = rowc[j];
+                    const float4 av = load4<ELT>(stages + __float_as_uint(rcj.y), sl);
+                    const float2 c2 = make_float2(rcj.x, rcj.x);
+                    const float2 lo = __ffma2_rn(c2, make_float2(av.x, av.y), make_float2(dd.x, dd.y));
+                    const float2 hi = __ffma2_rn(c2, make_float2(av.z, av.w), make_float2(dd.z, dd.w));
+                    dd = make_float4(lo.x, lo.y, hi.x, hi.y);
+                }
+                if (has_tail && sl == nl - 1) dd = zero_beyond(dd, rem);
+                const float4 v = xs[sl];
+                xs[sl] = make_float4(fmaf(dd.x, rq, v.x), fmaf(dd.y, rq, v.y), fmaf(dd.z, rq, v.z), fmaf(dd.w, rq, v.w));
+            }
+            __syncwarp();
+            // every warp read every row: this warp's release of the round's stages
+            for (int j = lane; j < q; j += 32) {
+                uint32_t par;
+                mbar_arrive(&empty[stage_of(j, par)]);
+            }
         }
         u += q;
         s0 += q;
         if (s0 >= S) { s0 -= S; ph0 ^= 1u; }
-        if (P > 1) {
-            named_bar_sync(1, NT);
-            for (int s = tid; s < nl; s += NT) {
-                float4 dd = dpart[s];
-                for (int pg = 1; pg < P; ++pg) {
-                    const float4 t = dpart[(size_t)pg * cp.chunk + s];
-                    dd.x += t.x; dd.y += t.y; dd.z += t.z; dd.w += t.w;
-                }
-                const float4 v = xs[s];
-                xs[s] = make_float4(fmaf(dd.x, rq, v.x), fmaf(dd.y, rq, v.y), fmaf(dd.z, rq, v.z), fmaf(dd.w, rq, v.w));
-            }
-        }
         named_bar_sync(1, NT);   // x complete for the next round's dots
         // ---- 5. convergence / divergence check (a second grid barrier) ----
         const int64_t done = r + 1;
@@ -627,8 +656,9 @@ int launch_colsplit_solve(const SolveArgs& a, const KParams& base, cudaStream_t 
     for (const CsVariant& v : kCsTab)
         if (v.elt == elt) var = &v;
     if (!var) return RK_EINVAL;
-    // row groups of the update: as many as keep every consumer thread on a slice
-    const int P = nt / chunk > 1 ? (nt / chunk < a.q ? nt / chunk : a.q) : 1;
+    // the update: a warp's own rows over chunks of at most 128 slices (no thread idle in
+    // a warp, stages released by their one reader), a thread's slices over all rows beyond
+    const bool warp_rows = chunk <= kCsWarpRowsL * 32;
     const uint32_t eb = pl->dt == RK_F32 ? 4u : (pl->dt == RK_BF16 ? 2u : 1u);
     // a stage holds one chunk (the kernel reads no slice past the CTA's own)
     const uint32_t stride = ((uint32_t)chunk * 4u * eb + 127u) & ~127u;
@@ -636,7 +666,7 @@ int launch_colsplit_solve(const SolveArgs& a, const KParams& base, cudaStream_t 
     // twice that lets the producer fetch the next round during the exchange
     int S = 0;
     while (S < 2 * a.q + kCsSpare && S < 252 &&
-           (size_t)(S + 1) * stride + cs_ctrl_bytes(S + 1, nt, chunk, P) <= (size_t)smem_max)
+           (size_t)(S + 1) * stride + cs_ctrl_bytes(S + 1, nt, chunk, warp_rows) <= (size_t)smem_max)
         ++S;
     S -= S % kCsProd;   // each producer warp serves its own stages
     if (S < a.q) return RK_EINVAL;   // the round's rows do not fit the shared memory
@@ -652,9 +682,9 @@ int launch_colsplit_solve(const SolveArgs& a, const KParams& base, cudaStream_t 
     cp.k.row_bytes = 0;   // per-CTA copy sizes are computed in the kernel
     cp.k.chkpart = a.V + ((part_floats + 3) & ~(size_t)3);
     cp.chunk = chunk;
-    cp.groups = P;
+    cp.warp_rows = warp_rows ? 1 : 0;
     cp.part = a.V;
-    const size_t smem = (size_t)S * stride + cs_ctrl_bytes(S, nt, chunk, P);
+    const size_t smem = (size_t)S * stride + cs_ctrl_bytes(S, nt, chunk, warp_rows);
     if (cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RK_ECUDA;
     void* args[] = {(void*)&cp};
