@@ -28,6 +28,7 @@ constexpr int kCsMaxQ = 64;    // workers a round (colsplit_fits in rk_internal.
 constexpr int kCsSpare = 8;    // ring stages beyond two rounds' rows
 constexpr int kCsProd = 4;     // producer warps (the ring's stage count is a multiple)
 constexpr int kCsWarpRowsL = 4;   // slices a lane in the warp-rows update (chunks <= 128 slices)
+constexpr int kCsSlicesAThread = 4;   // slices a thread in the rows-outer update (chunks <= 4 NT)
 
 struct CSParams {
     KParams k;
@@ -519,44 +520,96 @@ __global__ void __launch_bounds__(NT + 32 * kCsProd, 1) rka_colsplit_kernel(cons
                 xs[sl] = make_float4(fmaf(dd.x, rq, v.x), fmaf(dd.y, rq, v.y), fmaf(dd.z, rq, v.z), fmaf(dd.w, rq, v.w));
             }
         } else {
-            // slice s of every thread summed over all rows in ascending j, UJ rows a step
-            // with their coefficients and slices loaded together
+            // slices sl = tid + NT i of every thread, each summed over all rows in ascending j,
+            // UJ rows a step with their coefficients and slices loaded together
             constexpr int UJ = 8;
-            for (int sl = tid; sl < nl; sl += NT) {
-                float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
-                int j = 0;
-                for (; j + UJ <= q; j += UJ) {
+            if (nl <= kCsSlicesAThread * NT) {
+                // rows outer: after each step every warp has read the step's rows and
+                // releases their stages, so that the next round's copies can land while the
+                // update goes on (rings of one round, the widest chunks)
+                float4 dd[kCsSlicesAThread];
+#pragma unroll
+                for (int i = 0; i < kCsSlicesAThread; ++i) dd[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int j0 = 0; j0 < q; j0 += UJ) {
+                    const int jc = min(UJ, q - j0);   // rows of this step
                     float2 rcj[UJ];
-                    float4 av[UJ];
 #pragma unroll
-                    for (int e = 0; e < UJ; ++e) rcj[e] = rowc[j + e];
+                    for (int e = 0; e < UJ; ++e) rcj[e] = e < jc ? rowc[j0 + e] : make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int e = 0; e < UJ; ++e) av[e] = load4<ELT>(stages + __float_as_uint(rcj[e].y), sl);
+                    for (int i = 0; i < kCsSlicesAThread; ++i) {
+                        const int sl = tid + NT * i;
+                        if (sl < nl) {
+                            float4 av[UJ];
 #pragma unroll
-                    for (int e = 0; e < UJ; ++e) {
-                        const float2 c2 = make_float2(rcj[e].x, rcj[e].x);
-                        const float2 lo = __ffma2_rn(c2, make_float2(av[e].x, av[e].y), make_float2(dd.x, dd.y));
-                        const float2 hi = __ffma2_rn(c2, make_float2(av[e].z, av[e].w), make_float2(dd.z, dd.w));
-                        dd = make_float4(lo.x, lo.y, hi.x, hi.y);
+                            for (int e = 0; e < UJ; ++e)
+                                av[e] = e < jc ? load4<ELT>(stages + __float_as_uint(rcj[e].y), sl)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                            for (int e = 0; e < UJ; ++e) {
+                                if (e < jc) {
+                                    const float2 c2 = make_float2(rcj[e].x, rcj[e].x);
+                                    const float2 lo = __ffma2_rn(c2, make_float2(av[e].x, av[e].y),
+                                                                 make_float2(dd[i].x, dd[i].y));
+                                    const float2 hi = __ffma2_rn(c2, make_float2(av[e].z, av[e].w),
+                                                                 make_float2(dd[i].z, dd[i].w));
+                                    dd[i] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (lane < jc) {
+                        uint32_t par;
+                        mbar_arrive(&empty[stage_of(j0 + lane, par)]);
                     }
                 }
-                for (; j < q; ++j) {
-                    const float2 rcj = rowc[j];
-                    const float4 av = load4<ELT>(stages + __float_as_uint(rcj.y), sl);
-                    const float2 c2 = make_float2(rcj.x, rcj.x);
-                    const float2 lo = __ffma2_rn(c2, make_float2(av.x, av.y), make_float2(dd.x, dd.y));
-                    const float2 hi = __ffma2_rn(c2, make_float2(av.z, av.w), make_float2(dd.z, dd.w));
-                    dd = make_float4(lo.x, lo.y, hi.x, hi.y);
+#pragma unroll
+                for (int i = 0; i < kCsSlicesAThread; ++i) {
+                    const int sl = tid + NT * i;
+                    if (sl < nl) {
+                        if (has_tail && sl == nl - 1) dd[i] = zero_beyond(dd[i], rem);
+                        const float4 v = xs[sl];
+                        xs[sl] = make_float4(fmaf(dd[i].x, rq, v.x), fmaf(dd[i].y, rq, v.y), fmaf(dd[i].z, rq, v.z),
+                                             fmaf(dd[i].w, rq, v.w));
+                    }
                 }
-                if (has_tail && sl == nl - 1) dd = zero_beyond(dd, rem);
-                const float4 v = xs[sl];
-                xs[sl] = make_float4(fmaf(dd.x, rq, v.x), fmaf(dd.y, rq, v.y), fmaf(dd.z, rq, v.z), fmaf(dd.w, rq, v.w));
-            }
-            __syncwarp();
-            // every warp read every row: this warp's release of the round's stages
-            for (int j = lane; j < q; j += 32) {
-                uint32_t par;
-                mbar_arrive(&empty[stage_of(j, par)]);
+            } else {
+                for (int sl = tid; sl < nl; sl += NT) {
+                    float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
+                    int j = 0;
+                    for (; j + UJ <= q; j += UJ) {
+                        float2 rcj[UJ];
+                        float4 av[UJ];
+#pragma unroll
+                        for (int e = 0; e < UJ; ++e) rcj[e] = rowc[j + e];
+#pragma unroll
+                        for (int e = 0; e < UJ; ++e) av[e] = load4<ELT>(stages + __float_as_uint(rcj[e].y), sl);
+#pragma unroll
+                        for (int e = 0; e < UJ; ++e) {
+                            const float2 c2 = make_float2(rcj[e].x, rcj[e].x);
+                            const float2 lo = __ffma2_rn(c2, make_float2(av[e].x, av[e].y), make_float2(dd.x, dd.y));
+                            const float2 hi = __ffma2_rn(c2, make_float2(av[e].z, av[e].w), make_float2(dd.z, dd.w));
+                            dd = make_float4(lo.x, lo.y, hi.x, hi.y);
+                        }
+                    }
+                    for (; j < q; ++j) {
+                        const float2 rcj = rowc[j];
+                        const float4 av = load4<ELT>(stages + __float_as_uint(rcj.y), sl);
+                        const float2 c2 = make_float2(rcj.x, rcj.x);
+                        const float2 lo = __ffma2_rn(c2, make_float2(av.x, av.y), make_float2(dd.x, dd.y));
+                        const float2 hi = __ffma2_rn(c2, make_float2(av.z, av.w), make_float2(dd.z, dd.w));
+                        dd = make_float4(lo.x, lo.y, hi.x, hi.y);
+                    }
+                    if (has_tail && sl == nl - 1) dd = zero_beyond(dd, rem);
+                    const float4 v = xs[sl];
+                    xs[sl] = make_float4(fmaf(dd.x, rq, v.x), fmaf(dd.y, rq, v.y), fmaf(dd.z, rq, v.z), fmaf(dd.w, rq, v.w));
+                }
+                __syncwarp();
+                // every warp read every row: this warp's release of the round's stages
+                for (int j = lane; j < q; j += 32) {
+                    uint32_t par;
+                    mbar_arrive(&empty[stage_of(j, par)]);
+                }
             }
         }
         u += q;

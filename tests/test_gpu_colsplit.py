@@ -63,6 +63,19 @@ def test_colsplit_ragged_and_long_rows(rk, m, n):
     assert_close(x.cpu().numpy(), xo, TOL, what=f"{m}x{n}")
 
 
+def test_colsplit_very_long_rows(rk):
+    """Rows of 700001 columns (2.8 MB): chunks of 1152 slices a CTA, wider than the update's
+    rows-outer layout holds, so each thread sums its slices over all rows in turn."""
+    s = rk_inputs.gaussian_system(16, 700001, seed=11)
+    A = rk.aligned_rows(_dev(s.A))
+    plan = rk.rk_setup(A)
+    x, info = rk.rka_solve(plan, _dev(s.b), q=4, rounds=6, seed=5, omega=2.0, check_every=0)
+    assert info.status == 0
+    xo = oracle.rkab(s.A, s.b.astype(np.float64), np.zeros(700001), q=4, alpha=1, rounds=6, seed=5,
+                     tab=oracle.table(s.A), omega=2.0)
+    assert_close(x.cpu().numpy(), xo, TOL, what="700001 columns")
+
+
 @pytest.mark.parametrize("kind", ["bf16", "fp8"])
 def test_colsplit_stored_rows(rk, wide, kind):
     s, A, _, _ = wide
