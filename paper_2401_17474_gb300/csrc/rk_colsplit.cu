@@ -17,9 +17,10 @@
 //      projections of Eq. (rka_uni_weights), held in the difference form (for chunks
 //      of at most 128 slices each warp sums its own rows and the warp sums are added
 //      in a fixed order; beyond, each thread sums its slices over all rows).
-// The stages of a round are released after step 4, so the ring holds at least the
-// round's q rows; the producer fills the rest with the next round's rows. Checks
-// (criterion, divergence) add a second grid barrier on the rounds they run.
+// A stage is released in step 4 as soon as its readers are done with it (the warp
+// that owns the row, or every warp after each step of eight rows), so the ring holds
+// at least the round's q rows; the producer fills the rest with the next round's rows.
+// Checks (criterion, divergence) add a second grid barrier on the rounds they run.
 #include "rk_solve_kernel.cuh"
 
 namespace rk {
