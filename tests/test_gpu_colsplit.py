@@ -140,3 +140,19 @@ def test_colsplit_limits(rk, wide):
     assert e.value.code == -1
     with pytest.raises(rk.RkError):
         rk.rkab_solve(plan, _dev(s.b), q=4, alpha=3, rounds=1)   # RKAB on rows this long: clusters only
+
+
+def test_colsplit_wait_limit_ends_the_solve_with_a_status(rk, wide):
+    """The column-split kernel's device waits are bounded too: with a 1 us limit the first
+    wait for a row (a cold copy takes longer) runs out, every CTA winds down (the other CTAs
+    leave the grid barrier on the status word, the producers stop at what was consumed and
+    drain their copies) and the solve reports RK_ETIMEOUT; the same plan solves normally
+    afterwards."""
+    s, A, plan, tab = wide
+    x, info = rk.rka_solve(plan, _dev(s.b), q=16, rounds=5, seed=1, check_every=0, timeout_s=1e-6,
+                           raise_on_error=False)
+    torch.cuda.synchronize()
+    assert info.status == -4, info   # RK_ETIMEOUT
+    x, info = rk.rka_solve(plan, _dev(s.b), q=16, rounds=5, seed=1, check_every=0)
+    assert info.status == 0
+    assert torch.isfinite(x).all()
