@@ -95,6 +95,15 @@ struct CParams {
     int chunk;          // slices per CTA (multiple of 4)
 };
 
+// Thread 0, once every CTA of the cluster has stopped sending: wait (bounded) for the
+// receive buffer it armed last if it never saw that group's totals land.  Kept out of
+// line: it runs once a launch, and the solve loop's registers are not its concern.
+static __device__ __noinline__ void cluster_drain_receive(uint64_t* recvbar, volatile Ctrl* ctrl, uint64_t timeout_ns,
+                                                   int* status) {
+    const int pw = ctrl->pad;
+    if (pw & 4) wait_parity(&recvbar[pw & 1], (uint32_t)((pw >> 1) & 1), drain_limit_ns(timeout_ns), status);
+}
+
 template <int NT, int VPT, int ELT, int W>
 __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams cp) {
     static_assert(CGroup<W>::NV <= kNVP, "too many partial sums per group");
@@ -136,6 +145,7 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
         mbar_init(&recvbar[1], 1);
         ctrl->stop_t = total;
         ctrl->flag = 0;
+        ctrl->pad = 0;   // here: the receive buffer armed and not yet seen complete (4 | parity << 1 | buffer)
         fence_barrier_init();
     }
     __syncthreads();
@@ -265,7 +275,10 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
                 const int wc = (p.alpha - j) < W ? (int)(p.alpha - j) : W;
                 const int buf = (int)(grp & 1);
                 const uint32_t rpar = (uint32_t)((grp >> 1) & 1);
-                if (tid == 0) mbar_arrive_expect_tx(&recvbar[buf], csize * NV * 4u);
+                if (tid == 0) {
+                    mbar_arrive_expect_tx(&recvbar[buf], csize * NV * 4u);
+                    ctrl->pad = 4 | (int)(rpar << 1) | buf;
+                }
                 int sg[W];
                 bool got = true;
 #pragma unroll
@@ -328,6 +341,7 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
                 }
                 // wait for all CTAs' totals of this group, then sum them in rank order
                 if (!wait_parity(&recvbar[buf], rpar, p.timeout_ns, status)) got = false;
+                else if (tid == 0) ctrl->pad = 0;
                 float mytot = 0.f;
                 if (lane < NV) {
                     for (uint32_t c = 0; c < csize; ++c) mytot += recv[(buf * kClusterMax + (int)c) * kNVP + lane];
@@ -433,8 +447,14 @@ __global__ void __launch_bounds__(NT + 32, 1) rkab_cluster_kernel(const CParams 
         }
         if (tid == 0) ctrl->stop_t = t;
     }
-    // no CTA of the cluster leaves while another may still write to its shared memory
+    // no CTA of the cluster leaves while another may still write to its shared memory:
+    // once every CTA has stopped sending (the first cluster barrier), a receive buffer
+    // armed for a group whose totals did not all arrive (a wait that ran out) is waited
+    // for again, bounded, so that every total already sent has landed before the second
+    // barrier lets the CTAs go
     __syncwarp();
+    cluster_sync_all();
+    if (tid == 0) cluster_drain_receive(recvbar, ctrl, p.timeout_ns, status);
     cluster_sync_all();
 }
 

@@ -115,3 +115,20 @@ def test_adjoint_length_rows_match_oracle(rk, kind, m, n, alpha, shape):
     xo = oracle.rkab(low, s.b.astype(np.float64), np.zeros(n), q=q, alpha=alpha, rounds=3, seed=11,
                      tab=oracle.table(low))
     assert_close(x.cpu().numpy(), xo, TOL, what=f"{kind} {shape}")
+
+
+@pytest.mark.parametrize("C", [4, 16])
+def test_cluster_wait_limit_ends_the_solve_with_a_status(rk, C):
+    """The cluster kernel's device waits are bounded: with a 1 us limit the first wait for
+    a row runs out, the CTAs of every cluster wind down (a receive buffer armed for a group
+    whose totals never came is waited for again, bounded, before the cluster's CTAs leave)
+    and the solve reports RK_ETIMEOUT; the same plan solves normally afterwards."""
+    A_t, b_t, _ = rk_inputs.gaussian_system_torch(6000, 10000, seed=9, device="cuda")
+    plan = rk.rk_setup(A_t)
+    x, info = rk.rkab_solve(plan, b_t, q=3, alpha=40, rounds=3, seed=2, check_every=0, cluster_size=C,
+                            timeout_s=1e-6, raise_on_error=False)
+    torch.cuda.synchronize()
+    assert info.status == -4, info   # RK_ETIMEOUT
+    x, info = rk.rkab_solve(plan, b_t, q=3, alpha=40, rounds=3, seed=2, check_every=0, cluster_size=C)
+    assert info.status == 0
+    assert torch.isfinite(x).all()
