@@ -1,4 +1,6 @@
-"""Host logic of bench.py that needs no GPU: the size of the oracle's timed sample.
+"""Host logic of bench.py that needs no GPU: the size of the oracle's timed sample, the
+roofline's algorithmic bytes, and the recorded DRAM traffic that is used only for the kernel
+source it was measured on.
 
 The sample must stay bounded and close to its time target whatever the probes
 measure (a slow first call that pages A in, a noisy difference between probes)."""
@@ -68,3 +70,20 @@ def test_algorithmic_bytes_of_the_roofline():
     assert bench.algorithmic_bytes(n, 4864, 1, 85, 4, 152) == 85 * (4864 * per_proj + 3 * 152 * n * 4)
     # BF16 rows: 2 bytes an element
     assert bench.algorithmic_bytes(n, 132, 1, 1, 2) == 132 * (n * 2 + 20) + 3 * 132 * n * 4
+
+
+def test_recorded_traffic_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from an ncu record tied to a hash of the solve
+    kernel's source: the record is used while the hash matches the source as it is, and
+    ignored (traffic null) once the source has changed or when no record exists."""
+    monkeypatch.setattr(bench, "PROFILE_DIR", str(tmp_path))
+    assert bench.recorded_traffic("c2") is None                     # no record
+    h = bench.kernel_hash()
+    (tmp_path / "rkab_kernel_c2.txt").write_text(
+        "DRAM bytes of one launch\n"
+        f"traffic_bytes_per_proj 38995.2 src {h}\n")
+    assert bench.recorded_traffic("c2") == pytest.approx(38995.2)
+    (tmp_path / "rkab_kernel_c2.txt").write_text(
+        f"traffic_bytes_per_proj 38995.2 src {'0' * len(h)}\n")    # taken on other source
+    assert bench.recorded_traffic("c2") is None
+    assert len(h) == 12 and h == bench.kernel_hash()               # stable for unchanged source
